@@ -1,0 +1,370 @@
+// api.cu -- C-ABI entry points for the single-image filters, the workspace,
+// device info, error reporting and planning.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <tuple>
+
+#include "runtime.h"
+
+namespace hrm {
+
+// ---- errors -----------------------------------------------------------------
+static thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return HRM_ECUDA;
+}
+void clear_error() { g_err.clear(); }
+
+// ---- device info ----------------------------------------------------------------
+static std::mutex g_mu;
+static std::map<int, DeviceInfo> g_devs;
+
+const DeviceInfo& device_info() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_devs.find(dev);
+    if (it != g_devs.end()) return it->second;
+    DeviceInfo di;
+    di.device = dev;
+    cudaDeviceGetAttribute(&di.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&di.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&di.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&di.max_blocks_per_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    if (di.num_sms <= 0) di.num_sms = 1;
+    if (di.smem_per_sm <= 0) di.smem_per_sm = 100 * 1024;
+    if (di.smem_optin <= 0) di.smem_optin = 48 * 1024;
+    if (di.max_blocks_per_sm <= 0) di.max_blocks_per_sm = 16;
+    return g_devs[dev] = di;
+}
+
+// ---- workspace -----------------------------------------------------------------
+static std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+int workspace_for(cudaStream_t st, Workspace** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto key = std::make_pair(dev, st);
+    auto it = g_ws.find(key);
+    if (it != g_ws.end()) {
+        *out = &it->second;
+        return HRM_OK;
+    }
+    Workspace w;
+    const size_t bytes = sizeof(LevelDesc) * WS_MAX_DESC + sizeof(uint32_t) * 2 * 4096 + 256 + 64 * 4;
+    void* base = nullptr;
+    e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) return fail(HRM_ENOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+    unsigned char* p = (unsigned char*)base;
+    w.desc = (LevelDesc*)p;
+    p += sizeof(LevelDesc) * WS_MAX_DESC;
+    w.hist = (uint32_t*)p;
+    p += sizeof(uint32_t) * 2 * 4096;
+    w.err = (unsigned*)p;
+    p += 256;
+    w.counters = (unsigned*)p;
+    e = cudaMemset(base, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace memset");
+    *out = &(g_ws[key] = w);
+    return HRM_OK;
+}
+
+// ---- planning ----------------------------------------------------------------------
+static std::map<std::tuple<int, int, int, int, int, int, unsigned>, hrm_plan> g_plans;
+
+static std::tuple<int, int, int, int, int, int, unsigned> tkey(const ProblemKey& k) {
+    return std::make_tuple(k.dtype, k.dims, k.width, k.height, k.depth, k.radius, k.flags);
+}
+bool plan_lookup(const ProblemKey& k, hrm_plan* p) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_plans.find(tkey(k));
+    if (it == g_plans.end()) return false;
+    *p = it->second;
+    return true;
+}
+void plan_store(const ProblemKey& k, const hrm_plan& p) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_plans[tkey(k)] = p;
+}
+
+int slots_for(int tw, int r, size_t budget) {
+    const long nc = tw + 2L * r;
+    long avail = (long)budget - META_BYTES - (nc + 1) * 32;
+    long s = avail / (nc * 16);
+    if (s > MAX_SLOTS) s = MAX_SLOTS;
+    return (int)s;
+}
+
+Plan2D default_plan2d(int es, int W, int H, int r, const DeviceInfo& di) {
+    (void)es;
+    Plan2D p{};
+    p.path = r <= 2 ? 1 : 2;
+    p.ppl = W <= 64 ? 2 : 4;
+    const int tw = 32 * p.ppl;
+    // shared memory budget per warp: aim for ~6 resident warps per SM
+    size_t budget = (size_t)di.smem_per_sm / 6 - 1024;
+    int s = slots_for(tw, r, budget);
+    while (s < 4 && budget + 4096 <= (size_t)di.smem_optin) {
+        budget += 4096;
+        s = slots_for(tw, r, budget);
+    }
+    p.nslots = std::max(2, std::min(s, MAX_SLOTS));
+    const size_t smem = hist2d_smem_bytes(tw, r, p.nslots);
+    int wps = (int)(di.smem_per_sm / (smem + 1024));
+    wps = std::max(1, std::min(wps, di.max_blocks_per_sm));
+    const long tiles_x = (W + tw - 1) / tw;
+    const long target = (long)di.num_sms * wps * 2;
+    long sh = (H * tiles_x + target - 1) / target;
+    const long n = 2L * r + 1;
+    sh = std::max(sh, std::min(2 * n, 64L));
+    sh = std::max(sh, 8L);
+    sh = std::min(sh, (long)H);
+    p.sh = (int)std::max(1L, sh);
+    return p;
+}
+
+Plan2D resolve_plan2d(int dtype, int W, int H, int r, unsigned flags, const DeviceInfo& di) {
+    const int es = dtype == HRM_U16 ? 2 : 1;
+    Plan2D p = default_plan2d(es, W, H, r, di);
+    hrm_plan hp;
+    ProblemKey k{dtype, 2, W, H, 1, r, flags};
+    if (plan_lookup(k, &hp)) {
+        if (hp.tile_width == 64 || hp.tile_width == 128 || hp.tile_width == 256) p.ppl = hp.tile_width / 32;
+        if (hp.strip_height > 0) p.sh = std::min(hp.strip_height, H);
+        if (hp.slot_kbytes > 0) {
+            int s = slots_for(32 * p.ppl, r, (size_t)hp.slot_kbytes * 1024);
+            p.nslots = std::max(2, std::min(s, MAX_SLOTS));
+        }
+        if (hp.path == 1 || hp.path == 2) p.path = hp.path;
+    }
+    return p;
+}
+
+// ---- validation ---------------------------------------------------------------------
+static bool overlap(const void* a, size_t alen, const void* b, size_t blen) {
+    auto x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + blen && y < x + alen;
+}
+
+int validate2d(int dtype, const void* src, size_t sp, const void* dst, size_t dp, int W, int H,
+               int r, int rmax, int border, unsigned flags) {
+    if (dtype != HRM_U8 && dtype != HRM_U16) return fail(HRM_EINVAL, "dtype must be HRM_U8 or HRM_U16");
+    if (border != HRM_BORDER_REPLICATE) return fail(HRM_EINVAL, "only HRM_BORDER_REPLICATE is supported");
+    if (flags & ~(unsigned)HRM_ADAPTIVE) return fail(HRM_EINVAL, "unknown flag bits");
+    if (W < 0 || H < 0) return fail(HRM_EINVAL, "negative image size");
+    if (r < 0 || r > rmax) return fail(HRM_EINVAL, "radius out of range");
+    if (W == 0 || H == 0) return HRM_OK;
+    const size_t es = dtype == HRM_U16 ? 2 : 1;
+    if (!src || !dst) return fail(HRM_EINVAL, "null image pointer");
+    if (sp < W * es || dp < W * es) return fail(HRM_EINVAL, "pitch smaller than a row");
+    if (((uintptr_t)src | (uintptr_t)dst | sp | dp) % es) return fail(HRM_EINVAL, "misaligned pointer or pitch");
+    const size_t sl = (size_t)(H - 1) * sp + W * es, dl = (size_t)(H - 1) * dp + W * es;
+    if (overlap(src, sl, dst, dl)) return fail(HRM_EINVAL, "src and dst overlap");
+    return HRM_OK;
+}
+
+// ---- 2D filters -----------------------------------------------------------------------
+int filter2d_impl(int dtype, const void* src, size_t sp, void* dst, size_t dp, int W, int H, int r,
+                  long rank, unsigned flags, int drop_bits, const hrm_plan* force, cudaStream_t st) {
+    if (W == 0 || H == 0) return HRM_OK;
+    const int es = dtype == HRM_U16 ? 2 : 1;
+    const long n = 2L * r + 1, N = n * n;
+    if (rank < -1 || rank >= N) return fail(HRM_EINVAL, "rank out of range");
+    const bool median = rank < 0 || rank == (N - 1) / 2;
+    const uint32_t K = (uint32_t)(rank < 0 ? (N + 1) / 2 : rank + 1);
+    cudaError_t e;
+    if (r == 0) {
+        e = cudaMemcpy2DAsync(dst, dp, src, sp, (size_t)W * es, H, cudaMemcpyDeviceToDevice, st);
+        return e == cudaSuccess ? HRM_OK : cuda_fail(e, "cudaMemcpy2DAsync");
+    }
+    const DeviceInfo& di = device_info();
+    Plan2D p = resolve_plan2d(dtype, W, H, r, flags, di);
+    if (force) {
+        if (force->tile_width == 64 || force->tile_width == 128 || force->tile_width == 256) p.ppl = force->tile_width / 32;
+        if (force->strip_height > 0) p.sh = std::min(force->strip_height, H);
+        if (force->slot_kbytes > 0) p.nslots = std::max(2, std::min(slots_for(32 * p.ppl, r, (size_t)force->slot_kbytes * 1024), MAX_SLOTS));
+        if (force->path == 1 || force->path == 2) p.path = force->path;
+    }
+    if (p.path == 1 && r <= 2 && median && drop_bits == 0) {
+        e = launch_sortnet2d(es, r, src, sp, dst, dp, W, H, 32, st);
+        return e == cudaSuccess ? HRM_OK : cuda_fail(e, "sortnet launch");
+    }
+    Workspace* ws = nullptr;
+    int rc = workspace_for(st, &ws);
+    if (rc) return rc;
+    const bool adaptive = (flags & HRM_ADAPTIVE) != 0;
+    Hist2DJob job{};
+    job.src = (const unsigned char*)src;
+    job.sp = sp;
+    job.dst = (unsigned char*)dst;
+    job.dp = dp;
+    job.W = W;
+    job.H = H;
+    job.r = r;
+    job.K = K;
+    job.drop_bits = drop_bits;
+    job.elem = es;
+    job.err = ws->err;
+    if (es == 2 || adaptive) {
+        e = launch_levels(es, adaptive, src, sp, 0, W, H, 1, ws->desc, ws->hist, di.num_sms, st);
+        if (e != cudaSuccess) return cuda_fail(e, "level pre-pass launch");
+        job.desc = ws->desc;
+        job.fixed_shift = 0;
+    } else {
+        job.desc = nullptr;
+        job.fixed_shift = 4;
+    }
+    const int tw = 32 * p.ppl;
+    job.ppl = p.ppl;
+    job.sh = p.sh;
+    job.nslots = p.nslots;
+    job.tiles_x = (W + tw - 1) / tw;
+    job.ntiles = job.tiles_x * ((H + p.sh - 1) / p.sh);
+    const size_t smem = hist2d_smem_bytes(tw, r, p.nslots);
+    if (smem > (size_t)di.smem_optin)
+        return fail(HRM_ENOTSUP, "plan needs more shared memory than the device offers");
+    e = launch_hist2d(job, st);
+    return e == cudaSuccess ? HRM_OK : cuda_fail(e, "hist2d launch");
+}
+
+}  // namespace hrm
+
+using namespace hrm;
+
+extern "C" {
+
+int hrm_version(void) { return HRM_VERSION; }
+
+const char* hrm_last_error(void) { return g_err.c_str(); }
+
+int hrm_filter2d(int dtype, const void* src, size_t src_pitch, void* dst, size_t dst_pitch, int width,
+                 int height, int radius, int border, unsigned flags, void* stream) {
+    int rc = validate2d(dtype, src, src_pitch, dst, dst_pitch, width, height, radius,
+                        HRM_MAX_RADIUS_2D, border, flags);
+    if (rc) return rc;
+    return filter2d_impl(dtype, src, src_pitch, dst, dst_pitch, width, height, radius, -1, flags, 0,
+                         nullptr, (cudaStream_t)stream);
+}
+
+int hrm_rank_filter2d(int dtype, const void* src, size_t src_pitch, void* dst, size_t dst_pitch,
+                      int width, int height, int radius, long rank, int border, unsigned flags,
+                      void* stream) {
+    int rc = validate2d(dtype, src, src_pitch, dst, dst_pitch, width, height, radius,
+                        HRM_MAX_RADIUS_2D, border, flags);
+    if (rc) return rc;
+    const long n = 2L * radius + 1;
+    if (rank < 0 || rank >= n * n) return fail(HRM_EINVAL, "rank out of range");
+    return filter2d_impl(dtype, src, src_pitch, dst, dst_pitch, width, height, radius, rank, flags, 0,
+                         nullptr, (cudaStream_t)stream);
+}
+
+int hrm_filter2d_lowprec(int dtype, const void* src, size_t src_pitch, void* dst, size_t dst_pitch,
+                         int width, int height, int radius, int drop_bits, void* stream) {
+    int rc = validate2d(dtype, src, src_pitch, dst, dst_pitch, width, height, radius,
+                        HRM_MAX_RADIUS_2D, HRM_BORDER_REPLICATE, 0);
+    if (rc) return rc;
+    if (drop_bits < 0 || drop_bits > 12) return fail(HRM_EINVAL, "drop_bits must be in 0..12");
+    if (drop_bits == 0)
+        return filter2d_impl(dtype, src, src_pitch, dst, dst_pitch, width, height, radius, -1, 0, 0,
+                             nullptr, (cudaStream_t)stream);
+    hrm_plan force{0, 0, 0, 2};  // the early-stopping walk lives in the histogram kernel
+    return filter2d_impl(dtype, src, src_pitch, dst, dst_pitch, width, height, radius, -1, 0,
+                         drop_bits, &force, (cudaStream_t)stream);
+}
+
+int hrm_device_status(void* stream) {
+    Workspace* ws = nullptr;
+    int rc = workspace_for((cudaStream_t)stream, &ws);
+    if (rc) return rc;
+    unsigned host = 0;
+    cudaError_t e = cudaMemcpyAsync(&host, ws->err, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "device status");
+    if (host) {
+        cudaMemsetAsync(ws->err, 0, sizeof(unsigned), (cudaStream_t)stream);
+        cudaStreamSynchronize((cudaStream_t)stream);
+        return fail(HRM_EDEVICE, "kernel reported device error code " + std::to_string(host));
+    }
+    return HRM_OK;
+}
+
+int hrm_get_plan(int dtype, int dims, int width, int height, int depth, int radius, unsigned flags,
+                 hrm_plan* plan) {
+    if (!plan) return fail(HRM_EINVAL, "null plan");
+    if (dims != 2 && dims != 3) return fail(HRM_EINVAL, "dims must be 2 or 3");
+    ProblemKey k{dtype, dims, width, height, depth, radius, flags};
+    if (plan_lookup(k, plan)) return HRM_OK;
+    const DeviceInfo& di = device_info();
+    Plan2D p = default_plan2d(dtype == HRM_U16 ? 2 : 1, width, height, radius, di);
+    plan->tile_width = 32 * p.ppl;
+    plan->strip_height = p.sh;
+    plan->slot_kbytes = (int)((hist2d_smem_bytes(32 * p.ppl, radius, p.nslots) + 1023) / 1024);
+    plan->path = p.path;
+    return HRM_OK;
+}
+
+int hrm_set_plan(int dtype, int dims, int width, int height, int depth, int radius, unsigned flags,
+                 const hrm_plan* plan) {
+    if (!plan) return fail(HRM_EINVAL, "null plan");
+    if (dims != 2 && dims != 3) return fail(HRM_EINVAL, "dims must be 2 or 3");
+    if (plan->tile_width != 0 && plan->tile_width != 64 && plan->tile_width != 128 && plan->tile_width != 256)
+        return fail(HRM_EINVAL, "tile_width must be 64, 128 or 256");
+    if (plan->path < 0 || plan->path > 2) return fail(HRM_EINVAL, "path must be 0, 1 or 2");
+    plan_store(ProblemKey{dtype, dims, width, height, depth, radius, flags}, *plan);
+    return HRM_OK;
+}
+
+int hrm_plan_save(const char* path) {
+    if (!path) return fail(HRM_EINVAL, "null path");
+    std::ofstream f(path);
+    if (!f) return fail(HRM_EINVAL, std::string("cannot write ") + path);
+    std::lock_guard<std::mutex> lk(g_mu);
+    f << "# hrm plan cache v1: dtype dims width height depth radius flags tile_width strip_height slot_kbytes path\n";
+    for (auto& kv : g_plans) {
+        auto& k = kv.first;
+        auto& p = kv.second;
+        f << std::get<0>(k) << ' ' << std::get<1>(k) << ' ' << std::get<2>(k) << ' ' << std::get<3>(k) << ' '
+          << std::get<4>(k) << ' ' << std::get<5>(k) << ' ' << std::get<6>(k) << ' ' << p.tile_width << ' '
+          << p.strip_height << ' ' << p.slot_kbytes << ' ' << p.path << '\n';
+    }
+    return f ? HRM_OK : fail(HRM_EINVAL, "write failed");
+}
+
+int hrm_plan_load(const char* path) {
+    if (!path) return fail(HRM_EINVAL, "null path");
+    std::ifstream f(path);
+    if (!f) return fail(HRM_EINVAL, std::string("cannot read ") + path);
+    std::string line;
+    int nload = 0;
+    while (std::getline(f, line)) {
+        if (line.empty() || line[0] == '#') continue;
+        std::istringstream is(line);
+        ProblemKey k{};
+        hrm_plan p{};
+        if (!(is >> k.dtype >> k.dims >> k.width >> k.height >> k.depth >> k.radius >> k.flags >>
+              p.tile_width >> p.strip_height >> p.slot_kbytes >> p.path))
+            return fail(HRM_EINVAL, "malformed plan line: " + line);
+        plan_store(k, p);
+        ++nload;
+    }
+    return HRM_OK;
+}
+
+}  // extern "C"

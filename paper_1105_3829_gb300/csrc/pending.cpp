@@ -1,0 +1,18 @@
+// pending.cpp -- entry points whose implementation lands in a later unit.
+#include "../../include/hrm.h"
+
+extern "C" {
+int hrm_filter3d(int, const void*, size_t, size_t, void*, size_t, size_t, int, int, int, int, int, unsigned, void*) { return HRM_ENOTSUP; }
+int hrm_rank_filter3d(int, const void*, size_t, size_t, void*, size_t, size_t, int, int, int, int, long, int, unsigned, void*) { return HRM_ENOTSUP; }
+int hrm_filter_batch(const hrm_job*, int, void*) { return HRM_ENOTSUP; }
+int hrm_batch_graph_create(const hrm_job*, int, void*, hrm_batch_graph**) { return HRM_ENOTSUP; }
+int hrm_batch_graph_launch(hrm_batch_graph*, void*) { return HRM_ENOTSUP; }
+int hrm_batch_graph_destroy(hrm_batch_graph*) { return HRM_ENOTSUP; }
+int hrm_autotune(int, int, int, int, int, int, unsigned, void*, hrm_plan*) { return HRM_ENOTSUP; }
+int hrm_server_create(void*, size_t, int, int, hrm_server**) { return HRM_ENOTSUP; }
+int hrm_submit(hrm_server*, const hrm_request*, uint64_t*) { return HRM_ENOTSUP; }
+int hrm_poll(hrm_server*, uint64_t, int) { return HRM_ENOTSUP; }
+double hrm_ticket_latency_us(hrm_server*, uint64_t) { return -1.0; }
+int hrm_server_stats_get(hrm_server*, hrm_server_stats*) { return HRM_ENOTSUP; }
+int hrm_server_destroy(hrm_server*) { return HRM_ENOTSUP; }
+}

@@ -1,0 +1,71 @@
+// runtime.h -- host runtime shared by the C-ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+
+#include "../../include/hrm.h"
+#include "hist2d.cuh"
+#include "hist_common.cuh"
+
+namespace hrm {
+
+// Thread-local last-error message; returns `code` for convenient `return fail(...)`.
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+struct DeviceInfo {
+    int device = -1;
+    int num_sms = 0;
+    int smem_per_sm = 0;       // bytes
+    int smem_optin = 0;        // max dynamic smem per block (bytes)
+    int max_blocks_per_sm = 32;
+};
+const DeviceInfo& device_info();  // of the current device
+
+// Per-(device, stream) workspace: level descriptors, pre-pass histograms,
+// the device error word and the batch work counters.
+constexpr int WS_MAX_DESC = 4096;
+struct Workspace {
+    LevelDesc* desc = nullptr;   // WS_MAX_DESC descriptors
+    uint32_t* hist = nullptr;    // 2 * 4096 counters (reused by every pre-pass on this stream)
+    unsigned* err = nullptr;     // device error word
+    unsigned* counters = nullptr;  // 64 work counters for persistent kernels
+};
+int workspace_for(cudaStream_t st, Workspace** out);
+
+// Planning.
+struct Plan2D {
+    int ppl;      // pixels per lane (TW = 32 * ppl)
+    int sh;       // strip height
+    int nslots;   // slots per warp incl. root
+    int path;     // 1 = selection network, 2 = histogram
+};
+struct ProblemKey {
+    int dtype, dims, width, height, depth, radius;
+    unsigned flags;
+};
+bool plan_lookup(const ProblemKey& k, hrm_plan* p);
+void plan_store(const ProblemKey& k, const hrm_plan& p);
+Plan2D default_plan2d(int es, int W, int H, int r, const DeviceInfo& di);
+Plan2D resolve_plan2d(int dtype, int W, int H, int r, unsigned flags, const DeviceInfo& di);
+int slots_for(int tw, int r, size_t budget);
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_sortnet2d(int elem, int radius, const void* src, size_t sp, void* dst, size_t dp,
+                             int W, int H, int rows_per_warp, cudaStream_t st);
+cudaError_t launch_hist2d(const Hist2DJob& job, cudaStream_t st);
+cudaError_t launch_levels(int elem, bool adaptive, const void* src, size_t sp, size_t slice, int W,
+                          int H, int D, LevelDesc* desc, uint32_t* hist, int num_sms,
+                          cudaStream_t st);
+
+// Shared 2D entry (median / rank / reduced precision).
+int filter2d_impl(int dtype, const void* src, size_t sp, void* dst, size_t dp, int W, int H, int r,
+                  long rank, unsigned flags, int drop_bits, const hrm_plan* force, cudaStream_t st);
+int validate2d(int dtype, const void* src, size_t sp, const void* dst, size_t dp, int W, int H,
+               int r, int rmax, int border, unsigned flags);
+
+}  // namespace hrm

@@ -1,0 +1,162 @@
+"""GPU parity of the 2D filters against the CPU oracle (bit-exact).
+
+Every call goes through the C ABI (libhrm.so via the ctypes binding); the
+expected values come only from oracle/.  Sizes span several warp tiles
+(128-column tiles, strips of rows) with ragged right and bottom edges.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hrm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_3829_gb300 import hrm as h
+    h.lib()
+    return h
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _rand(shape, dt, seed, hi=None):
+    rng = np.random.default_rng(seed)
+    top = (256 if dt == np.uint8 else 65536) if hi is None else hi
+    return rng.integers(0, top, size=shape).astype(dt)
+
+
+def run2d(hrm, img, r, adaptive=False):
+    out = hrm.filter2d(_dev(img), r, adaptive=adaptive)
+    hrm.device_status()
+    return _host(out)
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 7, 12])
+def test_random_small(hrm, oracle, dt, r):
+    img = _rand((97, 301), dt, 1000 + r)
+    np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 37), (45, 1), (3, 5), (17, 129), (130, 257), (64, 64)])
+@pytest.mark.parametrize("r", [1, 2, 5, 20])
+def test_shapes_and_big_radius(hrm, oracle, shape, r):
+    img = _rand(shape, np.uint16, sum(shape) + r, hi=4096)
+    np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
+
+
+@pytest.mark.parametrize("r", [5, 15, 50])
+def test_xray_distribution(hrm, oracle, r):
+    from paper_1105_3829_gb300 import inputs
+    img = inputs.xray12_u16(203, 389, seed=7 + r)
+    np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
+
+
+@pytest.mark.parametrize("r", [15, 50])
+def test_lowkey_adaptive_equals_uniform(hrm, oracle, r):
+    from paper_1105_3829_gb300 import inputs
+    img = inputs.lowkey16_u16(150, 333, seed=11 + r)
+    exp = oracle.median2d(img, r)
+    np.testing.assert_array_equal(run2d(hrm, img, r, adaptive=False), exp)
+    np.testing.assert_array_equal(run2d(hrm, img, r, adaptive=True), exp)
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+def test_value_extremes(hrm, oracle, dt):
+    top = 255 if dt == np.uint8 else 65535
+    rng = np.random.default_rng(3)
+    img = rng.choice(np.array([0, 1, top - 1, top]), size=(70, 140)).astype(dt)
+    for r in (1, 2, 3, 9):
+        np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
+    const = np.full((40, 40), top, dt)
+    for r in (1, 4):
+        np.testing.assert_array_equal(run2d(hrm, const, r), const)
+    spike = np.zeros((50, 60), dt)
+    spike[25, 30] = top
+    for r in (1, 3):
+        np.testing.assert_array_equal(run2d(hrm, spike, r), oracle.median2d(spike, r))
+
+
+def test_effective_bit_depths(hrm, oracle):
+    for bits in (1, 3, 8, 12, 16):
+        img = _rand((61, 150), np.uint16, bits, hi=1 << bits)
+        for r in (3, 10):
+            np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
+
+
+def test_many_nodes_per_row(hrm, oracle):
+    # a steep diagonal ramp: every output of a row sits in a different leaf
+    yy, xx = np.mgrid[0:120, 0:300]
+    img = ((xx * 211 + yy * 17) % 65536).astype(np.uint16)
+    for r in (3, 6, 30):
+        np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
+    from paper_1105_3829_gb300 import inputs
+    sine = inputs.paper_sine(90, 260, period=25, bits=16)
+    np.testing.assert_array_equal(run2d(hrm, sine, 12), oracle.median2d(sine, 12))
+
+
+def test_pitched_views(hrm, oracle):
+    big = _rand((80, 300), np.uint16, 5, hi=4096)
+    src = _dev(big)[:, 7:250]          # row pitch 600 B, width 243, offset start
+    out_full = torch.zeros((80, 256), dtype=torch.uint16, device="cuda")
+    out = out_full[:, :243]
+    hrm.filter2d(src, 6, out=out)
+    res = _host(out_full)
+    np.testing.assert_array_equal(res[:, :243], oracle.median2d(big[:, 7:250], 6))
+    assert np.all(res[:, 243:] == 0), "padding of dst must stay untouched"
+
+
+@pytest.mark.parametrize("r", [1, 2, 4])
+def test_rank_filters(hrm, oracle, r):
+    img = _rand((77, 140), np.uint16, 40 + r, hi=5000)
+    n = 2 * r + 1
+    for rank in (0, n * n - 1, (n * n) // 3, (n * n - 1) // 2):
+        out = _host(hrm.rank_filter2d(_dev(img), r, rank))
+        np.testing.assert_array_equal(out, oracle.median2d(img, r, rank=rank))
+
+
+@pytest.mark.parametrize("s", [1, 4, 6])
+def test_lowprec_is_truncated_median(hrm, oracle, s):
+    img = _rand((90, 200), np.uint16, 50 + s, hi=4096)
+    exact = oracle.median2d(img, 7)
+    out = _host(hrm.filter2d_lowprec(_dev(img), 7, s))
+    np.testing.assert_array_equal(out, exact & np.uint16(~((1 << s) - 1) & 0xFFFF))
+
+
+def test_radius_zero_and_errors(hrm):
+    img = _rand((10, 12), np.uint8, 9)
+    np.testing.assert_array_equal(run2d(hrm, img, 0), img)
+    t = _dev(img)
+    with pytest.raises(hrm.HRMError) as e:
+        hrm.filter2d(t, 128)
+    assert e.value.code == hrm.HRM_EINVAL
+    with pytest.raises(hrm.HRMError):
+        hrm.filter2d(t, 3, out=t)  # in-place (overlap) is rejected
+    rc = hrm.hrm_filter2d(1, t.data_ptr(), 12, t.data_ptr() + 4096, 12, 12, 10, 1, 1, 0, None)
+    assert rc == hrm.HRM_EINVAL  # unknown border mode
+    rc = hrm.hrm_filter2d(1, t.data_ptr(), 12, t.data_ptr() + 4096, 12, 12, 10, 1, 0, 8, None)
+    assert rc == hrm.HRM_EINVAL  # unknown flag bits
+    assert hrm.hrm_filter2d(1, 0, 0, 0, 0, 0, 0, 3, 0, 0, None) == hrm.HRM_OK  # empty image
+
+
+@pytest.mark.parametrize("r", [5, 50])
+def test_full_size_xray_sampled(hrm, oracle, r):
+    """4096x4096 uint16 x-ray workload in the bench's launch configuration,
+    checked on a seeded sample of output points (plus all four corners)."""
+    from paper_1105_3829_gb300 import inputs
+    img = inputs.xray12_u16()
+    out = run2d(hrm, img, r)
+    rng = np.random.default_rng(r)
+    ys = np.concatenate([rng.integers(0, 4096, 300), [0, 0, 4095, 4095]])
+    xs = np.concatenate([rng.integers(0, 4096, 300), [0, 4095, 0, 4095]])
+    np.testing.assert_array_equal(out[ys, xs], oracle.points(img, r, ys, xs))
