@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: exact 2D median of a 4096x4096 uint16 (12-bit x-ray-like) image
+at radii 1, 5, 15 and 50 -- output Mpix/s against radius, fraction of the HBM
+roofline, p50/p99 per launch.
+
+One step filters the image once at every radius (the whole hot path: the
+selection network at r = 1, the level pre-pass plus the hierarchical
+histogram kernel at r >= 3).  L2 is flushed (a 512 MiB write) before every
+launch; launches are timed with CUDA events on the launching stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hrm|reference]
+
+Multi-GPU (torchrun, one process per GPU): every rank filters its own image
+(weak scaling, no data-path collective); the timing is the max over ranks.
+``--impl reference`` times the brute-force CPU oracle on the host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "output Mpix/s vs radius (uint16 4096^2, bit-exact) and % HBM roofline; p50/p99 ms"
+UNIT = "Mpix/s"
+RADII = (1, 5, 15, 50)
+SIDE = 4096
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---- clocks ------------------------------------------------------------------
+
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, index: str):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(REASONS, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- roofline traffic from a committed ncu summary ----------------------------
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1105_3829_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch recorded by profiles/traffic.json for the current
+    kernel sources (null when the sources changed since the capture)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("csrc_hash") != csrc_hash():
+        return None
+    return d.get("kernels", {}).get(kernel)
+
+
+# ---- CPU oracle on a bounded sample ---------------------------------------------
+
+def oracle_sample(img, budget_s: float, radii=RADII):
+    """Time the oracle on the same number P of random output points at every
+    radius (the GPU metric weights the radii equally), with P chosen so the
+    whole sample takes about budget_s seconds.  Returns (points, seconds,
+    threads)."""
+    import oracle
+    oracle.build()
+    threads = oracle.default_threads()
+    rng = np.random.default_rng(12345)
+    n0 = 16 * threads
+    cost = 0.0
+    for r in radii:  # calibration
+        ys, xs = rng.integers(0, img.shape[0], n0), rng.integers(0, img.shape[1], n0)
+        t0 = time.perf_counter()
+        oracle.points(img, r, ys, xs, threads=threads)
+        cost += (time.perf_counter() - t0) / n0
+    P = int(max(n0, min(5_000_000, budget_s / max(cost, 1e-9))))
+    tot_s = 0.0
+    for r in radii:
+        ys, xs = rng.integers(0, img.shape[0], P), rng.integers(0, img.shape[1], P)
+        t0 = time.perf_counter()
+        oracle.points(img, r, ys, xs, threads=threads)
+        tot_s += time.perf_counter() - t0
+    return P * len(radii), tot_s, threads
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    from paper_1105_3829_gb300 import inputs
+    img = inputs.xray12_u16(SIDE, SIDE)
+    step_budget = max(2.0, min(20.0, 90.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(img, step_budget / 4, radii=RADII)
+    pts, secs = 0, 0.0
+    threads = 1
+    for _ in range(args.steps):
+        p, s, threads = oracle_sample(img, step_budget, radii=RADII)
+        pts += p
+        secs += s
+    value = pts / secs / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+        "data": "synthetic",
+        "config": {"workload": "2D median, 4096x4096 uint16 12-bit x-ray mixture, radii 1/5/15/50",
+                   "radii": list(RADII), "width": SIDE, "height": SIDE},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "per step: random output points at each radius, ~%.0f s of CPU work "
+                                   "(brute-force gather + Quickselect per point)" % step_budget},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---- GPU arm ------------------------------------------------------------------------
+
+def main():
+    global RADII
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hrm", choices=["hrm", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=16.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--radii", default=",".join(map(str, RADII)),
+                    help="comma list; the default is the benchmark workload (profiling runs may narrow it)")
+    args = ap.parse_args()
+    RADII = tuple(int(x) for x in args.radii.split(","))
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    from __graft_entry__ import build
+    from paper_1105_3829_gb300 import hrm, inputs
+
+    if rank == 0 or ws == 1:
+        build()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+        build()
+    dev = torch.device("cuda", local)
+
+    img_np = inputs.xray12_u16(SIDE, SIDE, seed=inputs.seed_for(2, rank))
+    img = torch.from_numpy(img_np).to(dev)
+    outs = {r: torch.empty_like(img) for r in RADII}
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    npx = SIDE * SIDE
+
+    def step(events=None):
+        for r in RADII:
+            flush.fill_(r & 0xFF)
+            if events is not None:
+                events[r][0].record(stream)
+            hrm.filter2d(img, r, out=outs[r])
+            if events is not None:
+                events[r][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    hrm.device_status()
+
+    ev = [{r: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for r in RADII}
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = vis.split(",")[local].strip() if vis else str(local)
+    with ClockSampler(smi_index) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            step(ev[k])
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    if dist:
+        dist.barrier()
+    hrm.device_status()
+    times = {r: np.array([ev[k][r][0].elapsed_time(ev[k][r][1]) for k in range(args.steps)]) for r in RADII}
+    dev_ms_step = float(sum(times[r].sum() for r in RADII) / args.steps)
+    if dist:
+        t = torch.tensor([dev_ms_step, t_wall], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms_step, t_wall = float(t[0]), float(t[1])
+    value = ws * len(RADII) * npx / (dev_ms_step * 1e-3) / 1e6
+
+    # ---- end to end through host buffers (pinned), same workload ----
+    if args.no_e2e:
+        e2e_ms = float("nan")
+    else:
+        e2e_ms = run_e2e(args, img_np, img, outs, stream, hrm, dist, dev)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    return report(args, ws, times, dev_ms_step, value, t_wall, e2e_ms, clk, npx, dist, img_np)
+
+
+def run_e2e(args, img_np, img, outs, stream, hrm, dist, dev):
+    import torch
+    host_in = torch.from_numpy(img_np).pin_memory()
+    host_out = {r: torch.empty((SIDE, SIDE), dtype=torch.uint16).pin_memory() for r in RADII}
+    dev_in = torch.empty_like(img)
+
+    def e2e_step():
+        dev_in.copy_(host_in, non_blocking=True)
+        for r in RADII:
+            hrm.filter2d(dev_in, r, out=outs[r])
+            host_out[r].copy_(outs[r], non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t[0])
+    ok = all(np.array_equal(host_out[r].numpy(), outs[r].cpu().numpy()) for r in RADII)
+    if not ok:
+        raise SystemExit("e2e outputs differ from the device outputs")
+    return e2e_ms
+
+
+def report(args, ws, times, dev_ms_step, value, t_wall, e2e_ms, clk, npx, dist, img_np):
+    hbm_gbs, peak_kind = peaks()
+    per_radius = {}
+    for r in RADII:
+        t = times[r]
+        p50 = float(np.percentile(t, 50))
+        per_radius[str(r)] = {
+            "mpix_s": npx / (p50 * 1e-3) / 1e6,
+            "p50_ms": p50, "p99_ms": float(np.percentile(t, 99)),
+            "hbm_frac": (4.0 * npx / (p50 * 1e-3) / 1e9) / hbm_gbs,
+            "path": "selection network" if r <= 2 else "levels pre-pass + hierarchical histogram",
+        }
+    dom = max(RADII, key=lambda r: times[r].mean())
+    dom_ms = float(times[dom].mean())
+    achieved = 4.0 * npx / (dom_ms * 1e-3) / 1e9
+    kname = "hist2d r=%d" % dom if dom > 2 else "sortnet r=%d" % dom
+    launches_per_step = sum(1 if r <= 2 else 3 for r in RADII)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+        "config": {"workload": "2D median, 4096x4096 uint16 12-bit x-ray mixture (0.6 N(800,150) + "
+                               "0.4 N(3000,400), 1% salt/pepper), radii 1/5/15/50, replicate border",
+                   "radii": list(RADII), "width": SIDE, "height": SIDE, "parallelism": "dp%d" % ws,
+                   "l2": "flushed (512 MiB write) before every launch; ms_per_step is the sum of the "
+                         "launches' CUDA-event times, flushes excluded",
+                   "ms_per_step_wall_incl_flush": 1e3 * t_wall / args.steps},
+        "per_radius": per_radius,
+        "roofline": {"bound": "hbm", "kernel": kname + " (the hrm_filter2d call: level pre-pass + kernel)",
+                     "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
+                     "peak_kind": peak_kind, "traffic": traffic_for(kname),
+                     "algorithmic_bytes_per_launch": 4 * npx},
+        "gpu_launches": launches_per_step * args.steps,
+        "e2e": None if e2e_ms != e2e_ms else
+               {"value": ws * len(RADII) * npx / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": 2 * npx, "d2h_bytes_per_step": 2 * npx * len(RADII),
+                "ms_per_step": e2e_ms, "path": "pinned host -> device copy, hrm_filter2d at every radius, "
+                                              "device -> pinned host copy of every output"},
+        "clocks": clk.summary(),
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        pts, secs, threads = oracle_sample(img_np, args.cpu_budget, radii=RADII)
+        line["cpu_baseline"] = {"value": pts / secs / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": "%d random output points spread over radii 1/5/15/50 (~%.0f s): "
+                                          "brute-force gather + Quickselect per point" % (pts, secs)}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -103,56 +103,70 @@ void plan_store(const ProblemKey& k, const hrm_plan& p) {
     g_plans[tkey(k)] = p;
 }
 
-int slots_for(int tw, int r, size_t budget) {
+int counter_width(int dims, int r) {
+    const long n = 2L * r + 1;
+    return (dims == 3 && n * n > 255) ? 2 : 1;
+}
+
+int slots_for(int tw, int r, int cw, size_t budget) {
     const long nc = tw + 2L * r;
     long avail = (long)budget - META_BYTES - (nc + 1) * 32;
-    long s = avail / (nc * 16);
+    long s = avail / (nc * 16 * cw);
     if (s > MAX_SLOTS) s = MAX_SLOTS;
     return (int)s;
 }
 
-Plan2D default_plan2d(int es, int W, int H, int r, const DeviceInfo& di) {
-    (void)es;
-    Plan2D p{};
-    p.path = r <= 2 ? 1 : 2;
+PlanH default_plan(int dims, int W, int lines, int walk, int r, const DeviceInfo& di) {
+    PlanH p{};
+    p.path = (dims == 2 && r <= 2) ? 1 : 2;
+    p.cw = counter_width(dims, r);
     p.ppl = W <= 64 ? 2 : 4;
+    if (p.cw == 2 && p.ppl > 4) p.ppl = 4;
     const int tw = 32 * p.ppl;
     // shared memory budget per warp: aim for ~6 resident warps per SM
     size_t budget = (size_t)di.smem_per_sm / 6 - 1024;
-    int s = slots_for(tw, r, budget);
+    int s = slots_for(tw, r, p.cw, budget);
     while (s < 4 && budget + 4096 <= (size_t)di.smem_optin) {
         budget += 4096;
-        s = slots_for(tw, r, budget);
+        s = slots_for(tw, r, p.cw, budget);
     }
     p.nslots = std::max(2, std::min(s, MAX_SLOTS));
-    const size_t smem = hist2d_smem_bytes(tw, r, p.nslots);
+    const size_t smem = hist_smem_bytes(tw, r, p.nslots, p.cw);
     int wps = (int)(di.smem_per_sm / (smem + 1024));
     wps = std::max(1, std::min(wps, di.max_blocks_per_sm));
     const long tiles_x = (W + tw - 1) / tw;
     const long target = (long)di.num_sms * wps * 2;
-    long sh = (H * tiles_x + target - 1) / target;
+    long sh = (walk * tiles_x * (long)lines + target - 1) / target;
     const long n = 2L * r + 1;
     sh = std::max(sh, std::min(2 * n, 64L));
     sh = std::max(sh, 8L);
-    sh = std::min(sh, (long)H);
+    sh = std::min(sh, (long)walk);
     p.sh = (int)std::max(1L, sh);
     return p;
 }
 
-Plan2D resolve_plan2d(int dtype, int W, int H, int r, unsigned flags, const DeviceInfo& di) {
-    const int es = dtype == HRM_U16 ? 2 : 1;
-    Plan2D p = default_plan2d(es, W, H, r, di);
+static void apply_plan(PlanH& p, const hrm_plan& hp, int r, int walk) {
+    int ppl = p.ppl;
+    if (hp.tile_width == 64 || hp.tile_width == 128 || hp.tile_width == 256) ppl = hp.tile_width / 32;
+    if (p.cw == 2 && ppl > 4) ppl = 4;
+    p.ppl = ppl;
+    if (hp.strip_height > 0) p.sh = std::min(hp.strip_height, walk);
+    if (hp.slot_kbytes > 0)
+        p.nslots = std::max(2, std::min(slots_for(32 * p.ppl, r, p.cw, (size_t)hp.slot_kbytes * 1024), MAX_SLOTS));
+    if (hp.path == 1 || hp.path == 2) p.path = hp.path;
+}
+
+PlanH resolve_plan(int dtype, int dims, int W, int H, int D, int r, unsigned flags, const DeviceInfo& di,
+                   const hrm_plan* force) {
+    const int lines = dims == 3 ? H : 1;
+    const int walk = dims == 3 ? D : H;
+    PlanH p = default_plan(dims, W, lines, walk, r, di);
     hrm_plan hp;
-    ProblemKey k{dtype, 2, W, H, 1, r, flags};
-    if (plan_lookup(k, &hp)) {
-        if (hp.tile_width == 64 || hp.tile_width == 128 || hp.tile_width == 256) p.ppl = hp.tile_width / 32;
-        if (hp.strip_height > 0) p.sh = std::min(hp.strip_height, H);
-        if (hp.slot_kbytes > 0) {
-            int s = slots_for(32 * p.ppl, r, (size_t)hp.slot_kbytes * 1024);
-            p.nslots = std::max(2, std::min(s, MAX_SLOTS));
-        }
-        if (hp.path == 1 || hp.path == 2) p.path = hp.path;
-    }
+    if (plan_lookup(ProblemKey{dtype, dims, W, H, D, r, flags}, &hp)) apply_plan(p, hp, r, walk);
+    if (force) apply_plan(p, *force, r, walk);
+    // the shared-memory plan must fit the device
+    while (p.nslots > 2 && hist_smem_bytes(32 * p.ppl, r, p.nslots, p.cw) > (size_t)di.smem_optin) --p.nslots;
+    while (p.ppl > 2 && hist_smem_bytes(32 * p.ppl, r, p.nslots, p.cw) > (size_t)di.smem_optin) p.ppl /= 2;
     return p;
 }
 
@@ -162,85 +176,116 @@ static bool overlap(const void* a, size_t alen, const void* b, size_t blen) {
     return x < y + blen && y < x + alen;
 }
 
-int validate2d(int dtype, const void* src, size_t sp, const void* dst, size_t dp, int W, int H,
-               int r, int rmax, int border, unsigned flags) {
-    if (dtype != HRM_U8 && dtype != HRM_U16) return fail(HRM_EINVAL, "dtype must be HRM_U8 or HRM_U16");
+int validate(const Image& im, int r, int border, unsigned flags) {
+    if (im.dtype != HRM_U8 && im.dtype != HRM_U16) return fail(HRM_EINVAL, "dtype must be HRM_U8 or HRM_U16");
     if (border != HRM_BORDER_REPLICATE) return fail(HRM_EINVAL, "only HRM_BORDER_REPLICATE is supported");
     if (flags & ~(unsigned)HRM_ADAPTIVE) return fail(HRM_EINVAL, "unknown flag bits");
-    if (W < 0 || H < 0) return fail(HRM_EINVAL, "negative image size");
+    if (im.W < 0 || im.H < 0 || im.D < 0) return fail(HRM_EINVAL, "negative image size");
+    const int rmax = im.dims == 3 ? HRM_MAX_RADIUS_3D : HRM_MAX_RADIUS_2D;
     if (r < 0 || r > rmax) return fail(HRM_EINVAL, "radius out of range");
-    if (W == 0 || H == 0) return HRM_OK;
-    const size_t es = dtype == HRM_U16 ? 2 : 1;
-    if (!src || !dst) return fail(HRM_EINVAL, "null image pointer");
-    if (sp < W * es || dp < W * es) return fail(HRM_EINVAL, "pitch smaller than a row");
-    if (((uintptr_t)src | (uintptr_t)dst | sp | dp) % es) return fail(HRM_EINVAL, "misaligned pointer or pitch");
-    const size_t sl = (size_t)(H - 1) * sp + W * es, dl = (size_t)(H - 1) * dp + W * es;
-    if (overlap(src, sl, dst, dl)) return fail(HRM_EINVAL, "src and dst overlap");
+    if (im.W == 0 || im.H == 0 || im.D == 0) return HRM_OK;
+    const size_t es = im.dtype == HRM_U16 ? 2 : 1;
+    if (!im.src || !im.dst) return fail(HRM_EINVAL, "null image pointer");
+    if (im.sp < im.W * es || im.dp < im.W * es) return fail(HRM_EINVAL, "pitch smaller than a row");
+    if (((uintptr_t)im.src | (uintptr_t)im.dst | im.sp | im.dp) % es) return fail(HRM_EINVAL, "misaligned pointer or pitch");
+    size_t sl = (size_t)(im.H - 1) * im.sp + im.W * es, dl = (size_t)(im.H - 1) * im.dp + im.W * es;
+    if (im.dims == 3) {
+        if (im.sslice < (size_t)im.H * im.sp || im.dslice < (size_t)im.H * im.dp)
+            return fail(HRM_EINVAL, "slice pitch smaller than a slice");
+        if ((im.sslice | im.dslice) % es) return fail(HRM_EINVAL, "misaligned slice pitch");
+        sl += (size_t)(im.D - 1) * im.sslice;
+        dl += (size_t)(im.D - 1) * im.dslice;
+    }
+    if (overlap(im.src, sl, im.dst, dl)) return fail(HRM_EINVAL, "src and dst overlap");
     return HRM_OK;
 }
 
-// ---- 2D filters -----------------------------------------------------------------------
-int filter2d_impl(int dtype, const void* src, size_t sp, void* dst, size_t dp, int W, int H, int r,
-                  long rank, unsigned flags, int drop_bits, const hrm_plan* force, cudaStream_t st) {
-    if (W == 0 || H == 0) return HRM_OK;
-    const int es = dtype == HRM_U16 ? 2 : 1;
-    const long n = 2L * r + 1, N = n * n;
+// ---- filters ---------------------------------------------------------------------------
+int make_hist_job(const Image& im, int r, uint32_t K, unsigned flags, int drop_bits, const PlanH& p,
+                  const LevelDesc* desc, unsigned* err, HistJob* job) {
+    (void)flags;
+    const int es = im.dtype == HRM_U16 ? 2 : 1;
+    HistJob j{};
+    j.src = (const unsigned char*)im.src;
+    j.dst = (unsigned char*)im.dst;
+    j.s_row = im.sp;
+    j.s_slice = im.sslice;
+    j.d_row = im.dp;
+    j.d_slice = im.dslice;
+    j.W = im.W;
+    j.H = im.H;
+    j.D = im.dims == 3 ? im.D : 1;
+    j.dims = im.dims;
+    j.r = r;
+    j.K = K;
+    j.drop_bits = drop_bits;
+    j.elem = es;
+    j.err = err;
+    j.desc = desc;
+    j.fixed_shift = desc ? 0 : 4;
+    j.ppl = p.ppl;
+    j.cw = p.cw;
+    j.sh = p.sh;
+    j.nslots = p.nslots;
+    const int tw = 32 * p.ppl;
+    const int walk = im.dims == 3 ? im.D : im.H;
+    const int lines = im.dims == 3 ? im.H : 1;
+    j.tiles_x = (im.W + tw - 1) / tw;
+    const long nt = (long)j.tiles_x * lines * ((walk + p.sh - 1) / p.sh);
+    if (nt > 0x7FFFFFFFL) return fail(HRM_ENOTSUP, "too many tiles");
+    j.ntiles = (int)nt;
+    *job = j;
+    return HRM_OK;
+}
+
+static int copy_image(const Image& im, cudaStream_t st) {
+    const size_t es = im.dtype == HRM_U16 ? 2 : 1;
+    cudaError_t e = cudaSuccess;
+    if (im.dims == 2) {
+        e = cudaMemcpy2DAsync(im.dst, im.dp, im.src, im.sp, im.W * es, im.H, cudaMemcpyDeviceToDevice, st);
+    } else {
+        for (int z = 0; z < im.D && e == cudaSuccess; ++z)
+            e = cudaMemcpy2DAsync((unsigned char*)im.dst + z * im.dslice, im.dp,
+                                  (const unsigned char*)im.src + z * im.sslice, im.sp, im.W * es, im.H,
+                                  cudaMemcpyDeviceToDevice, st);
+    }
+    return e == cudaSuccess ? HRM_OK : cuda_fail(e, "cudaMemcpy2DAsync");
+}
+
+int filter_impl(const Image& im, int r, long rank, unsigned flags, int drop_bits, const hrm_plan* force,
+                cudaStream_t st) {
+    if (im.W == 0 || im.H == 0 || im.D == 0) return HRM_OK;
+    const int es = im.dtype == HRM_U16 ? 2 : 1;
+    const long n = 2L * r + 1, N = im.dims == 3 ? n * n * n : n * n;
     if (rank < -1 || rank >= N) return fail(HRM_EINVAL, "rank out of range");
     const bool median = rank < 0 || rank == (N - 1) / 2;
     const uint32_t K = (uint32_t)(rank < 0 ? (N + 1) / 2 : rank + 1);
-    cudaError_t e;
-    if (r == 0) {
-        e = cudaMemcpy2DAsync(dst, dp, src, sp, (size_t)W * es, H, cudaMemcpyDeviceToDevice, st);
-        return e == cudaSuccess ? HRM_OK : cuda_fail(e, "cudaMemcpy2DAsync");
-    }
+    if (r == 0) return copy_image(im, st);
     const DeviceInfo& di = device_info();
-    Plan2D p = resolve_plan2d(dtype, W, H, r, flags, di);
-    if (force) {
-        if (force->tile_width == 64 || force->tile_width == 128 || force->tile_width == 256) p.ppl = force->tile_width / 32;
-        if (force->strip_height > 0) p.sh = std::min(force->strip_height, H);
-        if (force->slot_kbytes > 0) p.nslots = std::max(2, std::min(slots_for(32 * p.ppl, r, (size_t)force->slot_kbytes * 1024), MAX_SLOTS));
-        if (force->path == 1 || force->path == 2) p.path = force->path;
-    }
-    if (p.path == 1 && r <= 2 && median && drop_bits == 0) {
-        e = launch_sortnet2d(es, r, src, sp, dst, dp, W, H, 32, st);
+    const PlanH p = resolve_plan(im.dtype, im.dims, im.W, im.H, im.D, r, flags, di, force);
+    cudaError_t e;
+    if (im.dims == 2 && p.path == 1 && r <= 2 && median && drop_bits == 0) {
+        e = launch_sortnet2d(es, r, im.src, im.sp, im.dst, im.dp, im.W, im.H, 32, st);
         return e == cudaSuccess ? HRM_OK : cuda_fail(e, "sortnet launch");
     }
     Workspace* ws = nullptr;
     int rc = workspace_for(st, &ws);
     if (rc) return rc;
     const bool adaptive = (flags & HRM_ADAPTIVE) != 0;
-    Hist2DJob job{};
-    job.src = (const unsigned char*)src;
-    job.sp = sp;
-    job.dst = (unsigned char*)dst;
-    job.dp = dp;
-    job.W = W;
-    job.H = H;
-    job.r = r;
-    job.K = K;
-    job.drop_bits = drop_bits;
-    job.elem = es;
-    job.err = ws->err;
+    const LevelDesc* desc = nullptr;
     if (es == 2 || adaptive) {
-        e = launch_levels(es, adaptive, src, sp, 0, W, H, 1, ws->desc, ws->hist, di.num_sms, st);
+        e = launch_levels(es, adaptive, im.src, im.sp, im.dims == 3 ? im.sslice : 0, im.W, im.H,
+                          im.dims == 3 ? im.D : 1, ws->desc, ws->hist, di.num_sms, st);
         if (e != cudaSuccess) return cuda_fail(e, "level pre-pass launch");
-        job.desc = ws->desc;
-        job.fixed_shift = 0;
-    } else {
-        job.desc = nullptr;
-        job.fixed_shift = 4;
+        desc = ws->desc;
     }
-    const int tw = 32 * p.ppl;
-    job.ppl = p.ppl;
-    job.sh = p.sh;
-    job.nslots = p.nslots;
-    job.tiles_x = (W + tw - 1) / tw;
-    job.ntiles = job.tiles_x * ((H + p.sh - 1) / p.sh);
-    const size_t smem = hist2d_smem_bytes(tw, r, p.nslots);
-    if (smem > (size_t)di.smem_optin)
+    HistJob job;
+    rc = make_hist_job(im, r, K, flags, drop_bits, p, desc, ws->err, &job);
+    if (rc) return rc;
+    if (hist_smem_bytes(32 * p.ppl, r, p.nslots, p.cw) > (size_t)di.smem_optin)
         return fail(HRM_ENOTSUP, "plan needs more shared memory than the device offers");
-    e = launch_hist2d(job, st);
-    return e == cudaSuccess ? HRM_OK : cuda_fail(e, "hist2d launch");
+    e = launch_hist(job, st);
+    return e == cudaSuccess ? HRM_OK : cuda_fail(e, "hist launch");
 }
 
 }  // namespace hrm
@@ -255,37 +300,52 @@ const char* hrm_last_error(void) { return g_err.c_str(); }
 
 int hrm_filter2d(int dtype, const void* src, size_t src_pitch, void* dst, size_t dst_pitch, int width,
                  int height, int radius, int border, unsigned flags, void* stream) {
-    int rc = validate2d(dtype, src, src_pitch, dst, dst_pitch, width, height, radius,
-                        HRM_MAX_RADIUS_2D, border, flags);
+    Image im{dtype, 2, src, dst, src_pitch, 0, dst_pitch, 0, width, height, 1};
+    int rc = validate(im, radius, border, flags);
     if (rc) return rc;
-    return filter2d_impl(dtype, src, src_pitch, dst, dst_pitch, width, height, radius, -1, flags, 0,
-                         nullptr, (cudaStream_t)stream);
+    return filter_impl(im, radius, -1, flags, 0, nullptr, (cudaStream_t)stream);
 }
 
 int hrm_rank_filter2d(int dtype, const void* src, size_t src_pitch, void* dst, size_t dst_pitch,
                       int width, int height, int radius, long rank, int border, unsigned flags,
                       void* stream) {
-    int rc = validate2d(dtype, src, src_pitch, dst, dst_pitch, width, height, radius,
-                        HRM_MAX_RADIUS_2D, border, flags);
+    Image im{dtype, 2, src, dst, src_pitch, 0, dst_pitch, 0, width, height, 1};
+    int rc = validate(im, radius, border, flags);
     if (rc) return rc;
     const long n = 2L * radius + 1;
     if (rank < 0 || rank >= n * n) return fail(HRM_EINVAL, "rank out of range");
-    return filter2d_impl(dtype, src, src_pitch, dst, dst_pitch, width, height, radius, rank, flags, 0,
-                         nullptr, (cudaStream_t)stream);
+    return filter_impl(im, radius, rank, flags, 0, nullptr, (cudaStream_t)stream);
+}
+
+int hrm_filter3d(int dtype, const void* src, size_t src_pitch, size_t src_slice_pitch, void* dst,
+                 size_t dst_pitch, size_t dst_slice_pitch, int width, int height, int depth, int radius,
+                 int border, unsigned flags, void* stream) {
+    Image im{dtype, 3, src, dst, src_pitch, src_slice_pitch, dst_pitch, dst_slice_pitch, width, height, depth};
+    int rc = validate(im, radius, border, flags);
+    if (rc) return rc;
+    return filter_impl(im, radius, -1, flags, 0, nullptr, (cudaStream_t)stream);
+}
+
+int hrm_rank_filter3d(int dtype, const void* src, size_t src_pitch, size_t src_slice_pitch, void* dst,
+                      size_t dst_pitch, size_t dst_slice_pitch, int width, int height, int depth,
+                      int radius, long rank, int border, unsigned flags, void* stream) {
+    Image im{dtype, 3, src, dst, src_pitch, src_slice_pitch, dst_pitch, dst_slice_pitch, width, height, depth};
+    int rc = validate(im, radius, border, flags);
+    if (rc) return rc;
+    const long n = 2L * radius + 1;
+    if (rank < 0 || rank >= n * n * n) return fail(HRM_EINVAL, "rank out of range");
+    return filter_impl(im, radius, rank, flags, 0, nullptr, (cudaStream_t)stream);
 }
 
 int hrm_filter2d_lowprec(int dtype, const void* src, size_t src_pitch, void* dst, size_t dst_pitch,
                          int width, int height, int radius, int drop_bits, void* stream) {
-    int rc = validate2d(dtype, src, src_pitch, dst, dst_pitch, width, height, radius,
-                        HRM_MAX_RADIUS_2D, HRM_BORDER_REPLICATE, 0);
+    Image im{dtype, 2, src, dst, src_pitch, 0, dst_pitch, 0, width, height, 1};
+    int rc = validate(im, radius, HRM_BORDER_REPLICATE, 0);
     if (rc) return rc;
     if (drop_bits < 0 || drop_bits > 12) return fail(HRM_EINVAL, "drop_bits must be in 0..12");
-    if (drop_bits == 0)
-        return filter2d_impl(dtype, src, src_pitch, dst, dst_pitch, width, height, radius, -1, 0, 0,
-                             nullptr, (cudaStream_t)stream);
+    if (drop_bits == 0) return filter_impl(im, radius, -1, 0, 0, nullptr, (cudaStream_t)stream);
     hrm_plan force{0, 0, 0, 2};  // the early-stopping walk lives in the histogram kernel
-    return filter2d_impl(dtype, src, src_pitch, dst, dst_pitch, width, height, radius, -1, 0,
-                         drop_bits, &force, (cudaStream_t)stream);
+    return filter_impl(im, radius, -1, 0, drop_bits, &force, (cudaStream_t)stream);
 }
 
 int hrm_device_status(void* stream) {
@@ -312,10 +372,10 @@ int hrm_get_plan(int dtype, int dims, int width, int height, int depth, int radi
     ProblemKey k{dtype, dims, width, height, depth, radius, flags};
     if (plan_lookup(k, plan)) return HRM_OK;
     const DeviceInfo& di = device_info();
-    Plan2D p = default_plan2d(dtype == HRM_U16 ? 2 : 1, width, height, radius, di);
+    PlanH p = resolve_plan(dtype, dims, width, height, depth, radius, flags, di, nullptr);
     plan->tile_width = 32 * p.ppl;
     plan->strip_height = p.sh;
-    plan->slot_kbytes = (int)((hist2d_smem_bytes(32 * p.ppl, radius, p.nslots) + 1023) / 1024);
+    plan->slot_kbytes = (int)((hist_smem_bytes(32 * p.ppl, radius, p.nslots, p.cw) + 1023) / 1024);
     plan->path = p.path;
     return HRM_OK;
 }

@@ -1,0 +1,48 @@
+// hist.cu -- launch wrappers for the hierarchical-histogram kernel (2D and 3D).
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hist_tile.cuh"
+
+namespace hrm {
+
+template <typename T, int PPL, int CW>
+__global__ void __launch_bounds__(32) hist_kernel(HistJob job) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    hist_tile<T, PPL, CW>(job, (int)blockIdx.x, smem);
+}
+
+template <typename T, int PPL, int CW>
+static cudaError_t launch_one(const HistJob& job, size_t smem, cudaStream_t st) {
+    auto fn = hist_kernel<T, PPL, CW>;
+    if (smem > 48 * 1024) {  // opt in per launch: the attribute is per device and cheap to set
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    fn<<<job.ntiles, 32, smem, st>>>(job);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_t(const HistJob& job, size_t smem, cudaStream_t st) {
+    if (job.cw == 1) {
+        switch (job.ppl) {
+            case 2: return launch_one<T, 2, 1>(job, smem, st);
+            case 4: return launch_one<T, 4, 1>(job, smem, st);
+            case 8: return launch_one<T, 8, 1>(job, smem, st);
+        }
+    } else if (job.cw == 2) {
+        switch (job.ppl) {
+            case 2: return launch_one<T, 2, 2>(job, smem, st);
+            case 4: return launch_one<T, 4, 2>(job, smem, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_hist(const HistJob& job, cudaStream_t st) {
+    const size_t smem = hist_smem_bytes(32 * job.ppl, job.r, job.nslots, job.cw);
+    return job.elem == 1 ? launch_t<uint8_t>(job, smem, st) : launch_t<uint16_t>(job, smem, st);
+}
+
+}  // namespace hrm

@@ -1,32 +1,37 @@
-// hist2d.cuh -- hierarchical recursive running median, 2D tile body.
+// hist_tile.cuh -- hierarchical recursive running median: one warp, one tile.
 //
-// One warp filters one tile: TW = 32*PPL output columns of a strip of rows,
-// walking down the strip (Section III, "column IOTs" slid vertically and the
-// window assembled from them horizontally).
+// A tile is a row of TW = 32*PPL outputs along x that the warp walks along
+// the "walk axis" (y for 2D images, z for 3D volumes): Section III, column
+// IOTs slid along the walk axis, the window IOT assembled across x.
 //
 // Per warp, in shared memory:
-//   * column histograms ("column IOTs") for the TW + 2r columns the tile's
-//     windows touch, at the 16-interval top level (the root node, always
-//     resident) and for a small LRU cache of deeper nodes ("slots").  A slot
-//     holds, for every column, the 16 child counts of one tree node.  Counts
-//     are bytes (a column holds n <= 255 values).
-//   * Moving down one row removes the leaving pixel and inserts the entering
-//     pixel of every column into every resident node on its path (Section
-//     III-B, add_value / remove_value: one +-1 per level).
-//   * The window counts of a node are sums of its column counts over the n
-//     columns of each output's window (Section III: window IOT =
-//     sum of column IOTs).  They are formed on demand, only for the nodes the
-//     walk actually visits (Section III, on-demand update).  When many outputs
-//     share a node, one prefix sum over the tile's columns serves all of them
-//     (the parallel form of the window recursion "+entering column -leaving
-//     column"); for small windows each output sums its n columns directly.
-//   * get_order_statistic (Section III) descends level by level: the window
-//     counts of the 16 children of the current node are searched with a
-//     binary descent for the child holding rank K, K is reduced by the counts
-//     to its left, and the walk continues in that child.  The value reached at
-//     the leaves is exactly the K-th smallest value of the window.
-//   * A node needed for the first time (a non-elementary update in the
-//     paper's terms) is built from the n staged input rows of every column.
+//   * "column" histograms for the TW + 2r columns the tile's windows touch.
+//     In 2D a column is the n pixels of image column x inside the window's
+//     rows; in 3D it is the n x n slab of voxels (rows y-r..y+r, slices
+//     z-r..z+r) at x, and the window is the sum of n such slabs -- the same
+//     recursion one dimension up (Section III, N-dimensional extension).
+//   * The 16-interval top level (the root node) is always resident; deeper
+//     nodes live in a small LRU cache of "slots".  A slot holds, for every
+//     column, the 16 child counts of one tree node (8-bit counters when a
+//     column holds <= 255 values, 16-bit otherwise).
+//   * Advancing one step along the walk axis removes the leaving layer and
+//     inserts the entering layer of every column into every resident node on
+//     the value's path (Section III-B, add_value / remove_value: one +-1 per
+//     level).  A layer is one pixel in 2D and n voxels in 3D.
+//   * The window counts of a node are the sums of its column counts over the n
+//     columns of each output's window (Section III: window IOT = sum of
+//     column IOTs).  They are formed on demand, only for nodes the walk visits
+//     (Section III, on-demand window update).  When many outputs share a node,
+//     one prefix sum over the tile's columns serves all of them (the parallel
+//     form of the window recursion "+entering column -leaving column"); when
+//     few do, each output sums its n columns directly.
+//   * get_order_statistic (Section III): at each level the window counts of
+//     the 16 children of the current node are searched by a binary descent for
+//     the child holding rank K; K drops by the counts to its left and the walk
+//     continues in that child.  The leaf reached is exactly the K-th smallest
+//     value of the window.
+//   * A node needed for the first time (the paper's non-elementary update) is
+//     built from the staged input values of every column.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -35,39 +40,103 @@
 
 namespace hrm {
 
-struct Hist2DJob {
+struct HistJob {
     const unsigned char* src;
-    size_t sp;
     unsigned char* dst;
-    size_t dp;
-    int W, H, r;
-    int sh;          // strip height (rows per tile)
-    int tiles_x;     // tiles per row of tiles
+    size_t s_row, s_slice;   // source pitches (bytes)
+    size_t d_row, d_slice;   // destination pitches (bytes)
+    int W, H, D;             // D = 1 for 2D
+    int dims;                // 2 or 3
+    int r;
+    int sh;                  // strip length along the walk axis
+    int tiles_x;             // tiles across x
     int ntiles;
-    uint32_t K;      // 1-based target rank
-    int nslots;      // slots per warp including the root
-    const LevelDesc* desc;  // nullptr: uniform with fixed_shift
+    uint32_t K;              // 1-based target rank
+    int nslots;              // slots per warp including the root
+    const LevelDesc* desc;   // nullptr: uniform with fixed_shift
     int fixed_shift;
-    int drop_bits;   // reduced precision: stop once <= drop_bits bits remain (0 = exact)
-    int elem;        // 1 or 2 (batch kernel dispatch)
-    int ppl;         // pixels per lane (batch kernel dispatch)
-    unsigned* err;   // device error word (may be null)
+    int drop_bits;           // reduced precision: stop once <= drop_bits bits remain (0 = exact)
+    int elem;                // 1 or 2 bytes per value
+    int ppl;                 // pixels per lane
+    int cw;                  // counter width in bytes (1 or 2)
+    unsigned* err;           // device error word (may be null)
 };
 
-__host__ __device__ inline size_t hist2d_smem_bytes(int tw, int r, int nslots) {
+__host__ __device__ inline size_t hist_smem_bytes(int tw, int r, int nslots, int cw) {
     int nc = tw + 2 * r;
-    return (size_t)META_BYTES + (size_t)(nc + 1) * 32 + (size_t)nslots * nc * 16;
+    return (size_t)META_BYTES + (size_t)(nc + 1) * 32 + (size_t)nslots * nc * 16 * cw;
 }
 
-template <typename T>
-__device__ __forceinline__ uint32_t ld2(const Hist2DJob& a, int y, int gx) {
-    return (uint32_t)__ldg(reinterpret_cast<const T*>(a.src + (size_t)y * a.sp) + gx);
+// ---- counter records (16 bins, CW bytes per bin) ---------------------------------
+
+template <int CW>
+__device__ __forceinline__ void rec_add(uint32_t (&a)[8], const unsigned char* rec) {
+    if (CW == 1) {
+        acc_add(a, *reinterpret_cast<const uint4*>(rec));
+    } else {
+        const uint4 q0 = reinterpret_cast<const uint4*>(rec)[0];
+        const uint4 q1 = reinterpret_cast<const uint4*>(rec)[1];
+        a[0] += q0.x; a[1] += q0.y; a[2] += q0.z; a[3] += q0.w;
+        a[4] += q1.x; a[5] += q1.y; a[6] += q1.z; a[7] += q1.w;
+    }
 }
 
-// Build slot s for node `key` at output row y from the n input rows of every column.
+template <int CW>
+__device__ __forceinline__ void rec_bump(unsigned char* rec, int b, int delta) {
+    uint32_t* w = reinterpret_cast<uint32_t*>(rec);
+    if (CW == 1) {
+        const uint32_t inc = 1u << (8 * (b & 3));
+        if (delta > 0) w[b >> 2] += inc; else w[b >> 2] -= inc;
+    } else {
+        const uint32_t inc = 1u << (16 * (b & 1));
+        if (delta > 0) w[b >> 1] += inc; else w[b >> 1] -= inc;
+    }
+}
+
+// Register counters used while building a record: 8 words (CW = 2) or the first 4 (CW = 1).
+template <int CW>
+__device__ __forceinline__ void reg_count(uint32_t (&c)[8], int b) {
+    if (CW == 1) {
+        const uint32_t inc = 1u << (8 * (b & 3));
+        const int w = b >> 2;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] += w == k ? inc : 0u;
+    } else {
+        const uint32_t inc = 1u << (16 * (b & 1));
+        const int w = b >> 1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c[k] += w == k ? inc : 0u;
+    }
+}
+
+template <int CW>
+__device__ __forceinline__ void rec_store(unsigned char* rec, const uint32_t (&c)[8]) {
+    uint4* q = reinterpret_cast<uint4*>(rec);
+    q[0] = make_uint4(c[0], c[1], c[2], c[3]);
+    if (CW == 2) q[1] = make_uint4(c[4], c[5], c[6], c[7]);
+}
+
+// ---- geometry -----------------------------------------------------------------
+
+struct Geo {
+    const unsigned char* src;
+    size_t tstride, istride;  // bytes per walk step / per layer index
+    int tmax, imax;           // clamp limits (walk axis, layer axis)
+    int ibase;                // first layer coordinate before clamping
+    int layer;                // values per column per walk step (1 in 2D, n in 3D)
+};
+
 template <typename T>
-__device__ void build_slot2d(const Hist2DJob& a, const Meta& m, unsigned char* slots, int NC,
-                             int x0, int y, int s, uint32_t key) {
+__device__ __forceinline__ uint32_t geo_ld(const Geo& g, int t, int i, int gx) {
+    const int tc = clampi(t, 0, g.tmax);
+    const int ic = clampi(g.ibase + i, 0, g.imax);
+    return (uint32_t)__ldg(reinterpret_cast<const T*>(g.src + (size_t)tc * g.tstride + (size_t)ic * g.istride) + gx);
+}
+
+// Build slot s for node `key` at walk position t from the staged values of every column.
+template <typename T, int CW>
+__device__ void build_slot(const HistJob& a, const Geo& g, const Meta& m, unsigned char* slots, int NC,
+                           int x0, int t, int s, uint32_t key) {
     const int lane = threadIdx.x & 31;
     const int r = a.r;
     const int level = (int)(key >> 20);
@@ -76,36 +145,39 @@ __device__ void build_slot2d(const Hist2DJob& a, const Meta& m, unsigned char* s
     uint32_t lo = 0, hi = 0xFFFFFFFFu;
     int dshift = 0;
     if (level > 0) {
-        int top = (int)m.D[c] - 4 * (level - 1);
-        int b = min(4, top);
+        const int top = (int)m.D[c] - 4 * (level - 1);
+        const int b = min(4, top);
         lo = m.e[c] + (pre << top);
         hi = min(lo + (1u << top), m.e[c + 1]);
         dshift = top - b;
     }
     for (int cx = lane; cx < NC; cx += 32) {
         const int gx = clampi(x0 - r + cx, 0, a.W - 1);
-        uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int tt = t - r; tt <= t + r; ++tt) {
 #pragma unroll 4
-        for (int yy = y - r; yy <= y + r; ++yy) {
-            uint32_t v = ld2<T>(a, clampi(yy, 0, a.H - 1), gx);
-            int d;
-            if (level == 0) {
-                d = coarse_of(m, v);
-            } else {
-                if (v < lo || v >= hi) continue;
-                d = (int)((v - lo) >> dshift);
+            for (int i = 0; i < g.layer; ++i) {
+                const uint32_t v = geo_ld<T>(g, tt, i, gx);
+                int d;
+                if (level == 0) {
+                    d = coarse_of(m, v);
+                } else {
+                    if (v < lo || v >= hi) continue;
+                    d = (int)((v - lo) >> dshift);
+                }
+                reg_count<CW>(cnt, d);
             }
-            reg_bump(c0, c1, c2, c3, d);
         }
-        *reinterpret_cast<uint4*>(slots + ((size_t)s * NC + cx) * 16) = make_uint4(c0, c1, c2, c3);
+        rec_store<CW>(slots + ((size_t)s * NC + cx) * 16 * CW, cnt);
     }
 }
 
-// Insert (delta = +1) or remove (-1) value v of column cx in every resident node on its path.
+// Insert (+1) or remove (-1) value v of column cx in every resident node on its path.
+template <int CW>
 __device__ __forceinline__ void column_update(const Meta& m, unsigned char* slots, int NC, int cx,
                                               uint32_t v, int delta) {
     const int c = coarse_of(m, v);
-    bump(reinterpret_cast<uint32_t*>(slots + (size_t)cx * 16), c, delta);
+    rec_bump<CW>(slots + (size_t)cx * 16 * CW, c, delta);
     if (!((m.lmask[0] >> c) & 1u)) return;
     const uint32_t u = v - m.e[c];
     const int D = (int)m.D[c];
@@ -116,11 +188,12 @@ __device__ __forceinline__ void column_update(const Meta& m, unsigned char* slot
         if (s < 0) continue;
         const int b = min(4, top);
         const int d = (int)((u >> (top - b)) & ((1u << b) - 1u));
-        bump(reinterpret_cast<uint32_t*>(slots + ((size_t)s * NC + cx) * 16), d, delta);
+        rec_bump<CW>(slots + ((size_t)s * NC + cx) * 16 * CW, d, delta);
     }
 }
 
 // Inclusive prefix over columns [lo, hi] of slot s into pfx[1 .. m], pfx[0] = 0.
+template <int CW>
 __device__ __forceinline__ void slot_prefix(const unsigned char* slots, uint4* pfx, int NC, int s,
                                             int lo, int hi) {
     const int lane = threadIdx.x & 31;
@@ -129,14 +202,13 @@ __device__ __forceinline__ void slot_prefix(const unsigned char* slots, uint4* p
     const int c_begin = lo + lane * q;
     const int c_end = min(c_begin + q, hi + 1);
     uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const uint4* col = reinterpret_cast<const uint4*>(slots) + (size_t)s * NC;
+    const unsigned char* base = slots + (size_t)s * NC * 16 * CW;
     for (int cx = c_begin; cx < c_end; ++cx) {
-        acc_add(acc, col[cx]);
+        rec_add<CW>(acc, base + (size_t)cx * 16 * CW);
         uint4* p = pfx + 2 * (cx - lo + 1);
         p[0] = make_uint4(acc[0], acc[1], acc[2], acc[3]);
         p[1] = make_uint4(acc[4], acc[5], acc[6], acc[7]);
     }
-    // exclusive scan of the chunk totals across lanes
     uint32_t inc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) inc[k] = acc[k];
@@ -144,7 +216,7 @@ __device__ __forceinline__ void slot_prefix(const unsigned char* slots, uint4* p
     for (int off = 1; off < 32; off <<= 1) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            uint32_t t = __shfl_up_sync(0xffffffffu, inc[k], off);
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc[k], off);
             if (lane >= off) inc[k] += t;
         }
     }
@@ -166,19 +238,46 @@ __device__ __forceinline__ void slot_prefix(const unsigned char* slots, uint4* p
     __syncwarp();
 }
 
-template <typename T, int PPL>
-__device__ void hist2d_tile(const Hist2DJob& a, int tile, unsigned char* sm) {
+template <typename T, int PPL, int CW>
+__device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     constexpr int TW = 32 * PPL;
     const int lane = threadIdx.x & 31;
     const int r = a.r;
     const int n = 2 * r + 1;
     const int NC = TW + 2 * r;
     const int S = a.nslots;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const int tx = tile % a.tiles_x;
+    const int rest = tile / a.tiles_x;
+    int yrow = 0, strip = rest;
+    if (a.dims == 3) {
+        yrow = rest % a.H;
+        strip = rest / a.H;
+    }
+    const int L = a.dims == 3 ? a.D : a.H;  // walk-axis length
     const int x0 = tx * TW;
-    const int ys = ty * a.sh;
-    const int ye = min(ys + a.sh, a.H);
-    if (ys >= a.H || x0 >= a.W) return;
+    const int ts = strip * a.sh;
+    const int te = min(ts + a.sh, L);
+    if (ts >= L || x0 >= a.W) return;
+
+    Geo g;
+    g.src = a.src;
+    if (a.dims == 3) {
+        g.tstride = a.s_slice;
+        g.istride = a.s_row;
+        g.tmax = a.D - 1;
+        g.imax = a.H - 1;
+        g.ibase = yrow - r;
+        g.layer = n;
+    } else {
+        g.tstride = a.s_row;
+        g.istride = 0;
+        g.tmax = a.H - 1;
+        g.imax = 0;
+        g.ibase = 0;
+        g.layer = 1;
+    }
+    unsigned char* drow0 = a.dst + (a.dims == 3 ? (size_t)yrow * a.d_row : 0);
+    const size_t dstep = a.dims == 3 ? a.d_slice : a.d_row;
 
     Meta& m = *reinterpret_cast<Meta*>(sm);
     uint4* pfx = reinterpret_cast<uint4*>(sm + META_BYTES);
@@ -192,33 +291,36 @@ __device__ void hist2d_tile(const Hist2DJob& a, int tile, unsigned char* sm) {
     }
     __syncwarp();
     rehash(m, S);
-    build_slot2d<T>(a, m, slots, NC, x0, ys, 0, 0u);
+    build_slot<T, CW>(a, g, m, slots, NC, x0, ts, 0, 0u);
     __syncwarp();
 
-    // direct vs shared-prefix cost model (warp instructions, see header comment)
-    const int prefix_cost = ((NC + 31) >> 5) * 31 + 120;
+    // cost model in warp instructions: one shared prefix vs direct n-column sums
+    const int prefix_cost = ((NC + 31) >> 5) * (CW == 1 ? 31 : 24) + 120;
+    const int direct_cost = n * (CW == 1 ? 17 : 10);
     uint32_t pass_id = 0;
 
-    for (int y = ys; y < ye; ++y) {
-        const uint32_t rowstamp = (uint32_t)(y - ys + 1);
-        if (y > ys) {
-            const int yo = clampi(y - r - 1, 0, a.H - 1);
-            const int yi = clampi(y + r, 0, a.H - 1);
-            if (yo != yi) {
+    for (int t = ts; t < te; ++t) {
+        const uint32_t stampv = (uint32_t)(t - ts + 1);
+        if (t > ts) {
+            const int to = clampi(t - r - 1, 0, L - 1);
+            const int ti = clampi(t + r, 0, L - 1);
+            if (to != ti) {
                 for (int cx = lane; cx < NC; cx += 32) {
                     const int gx = clampi(x0 - r + cx, 0, a.W - 1);
-                    const uint32_t vo = ld2<T>(a, yo, gx);
-                    const uint32_t vi = ld2<T>(a, yi, gx);
-                    if (vo != vi) {
-                        column_update(m, slots, NC, cx, vo, -1);
-                        column_update(m, slots, NC, cx, vi, +1);
+                    for (int i = 0; i < g.layer; ++i) {
+                        const uint32_t vo = geo_ld<T>(g, to, i, gx);
+                        const uint32_t vi = geo_ld<T>(g, ti, i, gx);
+                        if (vo != vi) {
+                            column_update<CW>(m, slots, NC, cx, vo, -1);
+                            column_update<CW>(m, slots, NC, cx, vi, +1);
+                        }
                     }
                 }
             }
             __syncwarp();
         }
 
-        // ---- level walk for the TW outputs of row y ----
+        // ---- level walk for the TW outputs at walk position t ----
         uint32_t K[PPL], pre[PPL], val[PPL];
         int cbin[PPL];
         bool pend[PPL];
@@ -244,6 +346,7 @@ __device__ void hist2d_tile(const Hist2DJob& a, int tile, unsigned char* sm) {
                 key[k] = level == 0 ? 0u : node_key(level, cbin[k], pre[k]);
                 todo[k] = pend[k];
                 dig[k] = 0;
+                slot[k] = -1;
             }
             for (int guard = 0;; ++guard) {
                 bool anyt = false;
@@ -289,11 +392,11 @@ __device__ void hist2d_tile(const Hist2DJob& a, int tile, unsigned char* sm) {
                     if (lane == 0) {
                         m.key[victim] = nk;
                         m.pin[victim] = pass_id;
-                        m.stamp[victim] = rowstamp;
+                        m.stamp[victim] = stampv;
                     }
                     __syncwarp();
                     rehash(m, S);
-                    build_slot2d<T>(a, m, slots, NC, x0, y, victim, nk);
+                    build_slot<T, CW>(a, g, m, slots, NC, x0, t, victim, nk);
 #pragma unroll
                     for (int k = 0; k < PPL; ++k)
                         if (todo[k] && slot[k] < 0 && key[k] == nk) slot[k] = victim;
@@ -314,15 +417,15 @@ __device__ void hist2d_tile(const Hist2DJob& a, int tile, unsigned char* sm) {
                 used = __reduce_or_sync(0xffffffffu, used);
                 const int maxres = (int)__reduce_max_sync(0xffffffffu, (unsigned)nres);
                 const int groups = __popc(used);
-                const bool direct = level > 0 && maxres * n * 17 < groups * prefix_cost;
+                const bool direct = level > 0 && maxres * direct_cost < groups * prefix_cost;
                 if (direct) {
 #pragma unroll
                     for (int k = 0; k < PPL; ++k) {
                         if (!res[k]) continue;
                         const int xl = lane + 32 * k;
-                        const uint4* col = reinterpret_cast<const uint4*>(slots) + (size_t)slot[k] * NC;
+                        const unsigned char* base = slots + (size_t)slot[k] * NC * 16 * CW;
                         uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                        for (int cx = xl; cx < xl + n; ++cx) acc_add(w, col[cx]);
+                        for (int cx = xl; cx < xl + n; ++cx) rec_add<CW>(w, base + (size_t)cx * 16 * CW);
                         dig[k] = select16(w, K[k]);
                     }
                 } else {
@@ -339,14 +442,14 @@ __device__ void hist2d_tile(const Hist2DJob& a, int tile, unsigned char* sm) {
                             }
                         lo = (int)__reduce_min_sync(0xffffffffu, (unsigned)lo);
                         hi = (int)__reduce_max_sync(0xffffffffu, (unsigned)(hi + 1)) - 1;
-                        slot_prefix(slots, pfx, NC, s, lo, hi + 2 * r);
+                        slot_prefix<CW>(slots, pfx, NC, s, lo, hi + 2 * r);
 #pragma unroll
                         for (int k = 0; k < PPL; ++k) {
                             if (!(res[k] && slot[k] == s)) continue;
                             const int xl = lane + 32 * k;
                             const uint4* pa = pfx + 2 * (xl - lo);
                             const uint4* pb = pfx + 2 * (xl - lo + n);
-                            uint4 a0 = pa[0], a1 = pa[1], b0 = pb[0], b1 = pb[1];
+                            const uint4 a0 = pa[0], a1 = pa[1], b0 = pb[0], b1 = pb[1];
                             uint32_t w[8] = {b0.x - a0.x, b0.y - a0.y, b0.z - a0.z, b0.w - a0.w,
                                              b1.x - a1.x, b1.y - a1.y, b1.z - a1.z, b1.w - a1.w};
                             dig[k] = select16(w, K[k]);
@@ -357,7 +460,7 @@ __device__ void hist2d_tile(const Hist2DJob& a, int tile, unsigned char* sm) {
 #pragma unroll
                 for (int k = 0; k < PPL; ++k)
                     if (res[k]) {
-                        if (slot[k] > 0) m.stamp[slot[k]] = rowstamp;
+                        if (slot[k] > 0) m.stamp[slot[k]] = stampv;
                         todo[k] = false;
                     }
                 __syncwarp();
@@ -368,14 +471,14 @@ __device__ void hist2d_tile(const Hist2DJob& a, int tile, unsigned char* sm) {
                 if (!pend[k]) continue;
                 if (level == 0) {
                     cbin[k] = dig[k];
-                    const int D = (int)m.D[dig[k]];
-                    if (D <= a.drop_bits) {
+                    const int Dc = (int)m.D[dig[k]];
+                    if (Dc <= a.drop_bits) {
                         val[k] = m.e[dig[k]];
                         pend[k] = false;
                     }
                 } else {
-                    const int D = (int)m.D[cbin[k]];
-                    const int top = D - 4 * (level - 1);
+                    const int Dc = (int)m.D[cbin[k]];
+                    const int top = Dc - 4 * (level - 1);
                     const int b = min(4, top);
                     pre[k] = (pre[k] << b) | (uint32_t)dig[k];
                     const int left = top - b;
@@ -386,8 +489,8 @@ __device__ void hist2d_tile(const Hist2DJob& a, int tile, unsigned char* sm) {
                 }
             }
         }
-        // ---- store row y ----
-        T* drow = reinterpret_cast<T*>(a.dst + (size_t)y * a.dp);
+        // ---- store the outputs of walk position t ----
+        T* drow = reinterpret_cast<T*>(drow0 + (size_t)t * dstep);
         const uint32_t mask = a.drop_bits > 0 ? ~((1u << a.drop_bits) - 1u) : 0xFFFFFFFFu;
 #pragma unroll
         for (int k = 0; k < PPL; ++k) {

@@ -2,8 +2,6 @@
 #include "../../include/hrm.h"
 
 extern "C" {
-int hrm_filter3d(int, const void*, size_t, size_t, void*, size_t, size_t, int, int, int, int, int, unsigned, void*) { return HRM_ENOTSUP; }
-int hrm_rank_filter3d(int, const void*, size_t, size_t, void*, size_t, size_t, int, int, int, int, long, int, unsigned, void*) { return HRM_ENOTSUP; }
 int hrm_filter_batch(const hrm_job*, int, void*) { return HRM_ENOTSUP; }
 int hrm_batch_graph_create(const hrm_job*, int, void*, hrm_batch_graph**) { return HRM_ENOTSUP; }
 int hrm_batch_graph_launch(hrm_batch_graph*, void*) { return HRM_ENOTSUP; }

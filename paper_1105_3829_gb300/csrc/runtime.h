@@ -7,7 +7,7 @@
 #include <string>
 
 #include "../../include/hrm.h"
-#include "hist2d.cuh"
+#include "hist_tile.cuh"
 #include "hist_common.cuh"
 
 namespace hrm {
@@ -38,11 +38,12 @@ struct Workspace {
 int workspace_for(cudaStream_t st, Workspace** out);
 
 // Planning.
-struct Plan2D {
+struct PlanH {
     int ppl;      // pixels per lane (TW = 32 * ppl)
-    int sh;       // strip height
+    int sh;       // strip length along the walk axis
     int nslots;   // slots per warp incl. root
     int path;     // 1 = selection network, 2 = histogram
+    int cw;       // counter width (bytes)
 };
 struct ProblemKey {
     int dtype, dims, width, height, depth, radius;
@@ -50,22 +51,34 @@ struct ProblemKey {
 };
 bool plan_lookup(const ProblemKey& k, hrm_plan* p);
 void plan_store(const ProblemKey& k, const hrm_plan& p);
-Plan2D default_plan2d(int es, int W, int H, int r, const DeviceInfo& di);
-Plan2D resolve_plan2d(int dtype, int W, int H, int r, unsigned flags, const DeviceInfo& di);
-int slots_for(int tw, int r, size_t budget);
+// dims 2: lines = 1, walk = H; dims 3: lines = H (one tile row per y), walk = D.
+PlanH default_plan(int dims, int W, int lines, int walk, int r, const DeviceInfo& di);
+PlanH resolve_plan(int dtype, int dims, int W, int H, int D, int r, unsigned flags, const DeviceInfo& di,
+                   const hrm_plan* force);
+int slots_for(int tw, int r, int cw, size_t budget);
+int counter_width(int dims, int r);
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_sortnet2d(int elem, int radius, const void* src, size_t sp, void* dst, size_t dp,
                              int W, int H, int rows_per_warp, cudaStream_t st);
-cudaError_t launch_hist2d(const Hist2DJob& job, cudaStream_t st);
+cudaError_t launch_hist(const HistJob& job, cudaStream_t st);
 cudaError_t launch_levels(int elem, bool adaptive, const void* src, size_t sp, size_t slice, int W,
                           int H, int D, LevelDesc* desc, uint32_t* hist, int num_sms,
                           cudaStream_t st);
 
-// Shared 2D entry (median / rank / reduced precision).
-int filter2d_impl(int dtype, const void* src, size_t sp, void* dst, size_t dp, int W, int H, int r,
-                  long rank, unsigned flags, int drop_bits, const hrm_plan* force, cudaStream_t st);
-int validate2d(int dtype, const void* src, size_t sp, const void* dst, size_t dp, int W, int H,
-               int r, int rmax, int border, unsigned flags);
+// Shared entry (2D / 3D, median / rank / reduced precision).
+struct Image {
+    int dtype, dims;
+    const void* src;
+    void* dst;
+    size_t sp, sslice, dp, dslice;
+    int W, H, D;
+};
+int filter_impl(const Image& im, int r, long rank, unsigned flags, int drop_bits, const hrm_plan* force,
+                cudaStream_t st);
+int validate(const Image& im, int r, int border, unsigned flags);
+// Fill a HistJob (pre-pass descriptor supplied by the caller) for one image.
+int make_hist_job(const Image& im, int r, uint32_t K, unsigned flags, int drop_bits, const PlanH& p,
+                  const LevelDesc* desc, unsigned* err, HistJob* job);
 
 }  // namespace hrm
