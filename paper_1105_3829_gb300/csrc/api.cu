@@ -116,22 +116,35 @@ int slots_for(int tw, int r, int cw, size_t budget) {
     return (int)s;
 }
 
-PlanH default_plan(int dims, int W, int lines, int walk, int r, const DeviceInfo& di) {
+size_t plan_smem(const PlanH& p, int r) {
+    return hist_smem_bytes(32 * p.ppl, r, p.nslots, p.cw, p.ring, p.es);
+}
+
+// Fill slots (and the ring decision) for a given per-warp shared-memory budget.
+static void size_slots(PlanH& p, int dims, int r, size_t budget) {
+    const int tw = 32 * p.ppl;
+    const size_t ring = hist_ring_bytes(tw, r, p.es);
+    p.ring = (dims == 2 && ring * 3 <= budget) ? 1 : 0;
+    const size_t rest = budget - (p.ring ? ring : 0);
+    p.nslots = std::max(2, std::min(slots_for(tw, r, p.cw, rest), MAX_SLOTS));
+}
+
+PlanH default_plan(int dims, int es, int W, int lines, int walk, int r, const DeviceInfo& di) {
     PlanH p{};
+    p.es = es;
     p.path = (dims == 2 && r <= 2) ? 1 : 2;
     p.cw = counter_width(dims, r);
-    p.ppl = W <= 64 ? 2 : 4;
-    if (p.cw == 2 && p.ppl > 4) p.ppl = 4;
+    // narrow tiles at small radii keep the per-row node working set in the slot cache
+    p.ppl = (W <= 64 || r <= 16) ? 2 : 4;
     const int tw = 32 * p.ppl;
     // shared memory budget per warp: aim for ~6 resident warps per SM
     size_t budget = (size_t)di.smem_per_sm / 6 - 1024;
-    int s = slots_for(tw, r, p.cw, budget);
-    while (s < 4 && budget + 4096 <= (size_t)di.smem_optin) {
+    size_slots(p, dims, r, budget);
+    while (p.nslots < 4 && budget + 4096 <= (size_t)di.smem_optin) {
         budget += 4096;
-        s = slots_for(tw, r, p.cw, budget);
+        size_slots(p, dims, r, budget);
     }
-    p.nslots = std::max(2, std::min(s, MAX_SLOTS));
-    const size_t smem = hist_smem_bytes(tw, r, p.nslots, p.cw);
+    const size_t smem = plan_smem(p, r);
     int wps = (int)(di.smem_per_sm / (smem + 1024));
     wps = std::max(1, std::min(wps, di.max_blocks_per_sm));
     const long tiles_x = (W + tw - 1) / tw;
@@ -145,14 +158,12 @@ PlanH default_plan(int dims, int W, int lines, int walk, int r, const DeviceInfo
     return p;
 }
 
-static void apply_plan(PlanH& p, const hrm_plan& hp, int r, int walk) {
-    int ppl = p.ppl;
-    if (hp.tile_width == 64 || hp.tile_width == 128 || hp.tile_width == 256) ppl = hp.tile_width / 32;
-    if (p.cw == 2 && ppl > 4) ppl = 4;
-    p.ppl = ppl;
+static void apply_plan(PlanH& p, const hrm_plan& hp, int dims, int r, int walk) {
+    if (hp.tile_width == 64 || hp.tile_width == 128 || hp.tile_width == 256) p.ppl = hp.tile_width / 32;
+    if (p.cw == 2 && p.ppl > 4) p.ppl = 4;
     if (hp.strip_height > 0) p.sh = std::min(hp.strip_height, walk);
-    if (hp.slot_kbytes > 0)
-        p.nslots = std::max(2, std::min(slots_for(32 * p.ppl, r, p.cw, (size_t)hp.slot_kbytes * 1024), MAX_SLOTS));
+    if (hp.slot_kbytes > 0) size_slots(p, dims, r, (size_t)hp.slot_kbytes * 1024);
+    else size_slots(p, dims, r, plan_smem(p, r));
     if (hp.path == 1 || hp.path == 2) p.path = hp.path;
 }
 
@@ -160,13 +171,15 @@ PlanH resolve_plan(int dtype, int dims, int W, int H, int D, int r, unsigned fla
                    const hrm_plan* force) {
     const int lines = dims == 3 ? H : 1;
     const int walk = dims == 3 ? D : H;
-    PlanH p = default_plan(dims, W, lines, walk, r, di);
+    const int es = dtype == HRM_U16 ? 2 : 1;
+    PlanH p = default_plan(dims, es, W, lines, walk, r, di);
     hrm_plan hp;
-    if (plan_lookup(ProblemKey{dtype, dims, W, H, D, r, flags}, &hp)) apply_plan(p, hp, r, walk);
-    if (force) apply_plan(p, *force, r, walk);
+    if (plan_lookup(ProblemKey{dtype, dims, W, H, D, r, flags}, &hp)) apply_plan(p, hp, dims, r, walk);
+    if (force) apply_plan(p, *force, dims, r, walk);
     // the shared-memory plan must fit the device
-    while (p.nslots > 2 && hist_smem_bytes(32 * p.ppl, r, p.nslots, p.cw) > (size_t)di.smem_optin) --p.nslots;
-    while (p.ppl > 2 && hist_smem_bytes(32 * p.ppl, r, p.nslots, p.cw) > (size_t)di.smem_optin) p.ppl /= 2;
+    while (p.nslots > 2 && plan_smem(p, r) > (size_t)di.smem_optin) --p.nslots;
+    if (plan_smem(p, r) > (size_t)di.smem_optin) p.ring = 0;
+    while (p.ppl > 2 && plan_smem(p, r) > (size_t)di.smem_optin) p.ppl /= 2;
     return p;
 }
 
@@ -189,7 +202,7 @@ int validate(const Image& im, int r, int border, unsigned flags) {
     if (im.sp < im.W * es || im.dp < im.W * es) return fail(HRM_EINVAL, "pitch smaller than a row");
     if (((uintptr_t)im.src | (uintptr_t)im.dst | im.sp | im.dp) % es) return fail(HRM_EINVAL, "misaligned pointer or pitch");
     size_t sl = (size_t)(im.H - 1) * im.sp + im.W * es, dl = (size_t)(im.H - 1) * im.dp + im.W * es;
-    if (im.dims == 3) {
+    if (im.dims == 3 && im.D > 1) {  // a single slice never uses its slice pitch
         if (im.sslice < (size_t)im.H * im.sp || im.dslice < (size_t)im.H * im.dp)
             return fail(HRM_EINVAL, "slice pitch smaller than a slice");
         if ((im.sslice | im.dslice) % es) return fail(HRM_EINVAL, "misaligned slice pitch");
@@ -227,6 +240,7 @@ int make_hist_job(const Image& im, int r, uint32_t K, unsigned flags, int drop_b
     j.cw = p.cw;
     j.sh = p.sh;
     j.nslots = p.nslots;
+    j.ring = p.ring;
     const int tw = 32 * p.ppl;
     const int walk = im.dims == 3 ? im.D : im.H;
     const int lines = im.dims == 3 ? im.H : 1;
@@ -282,7 +296,7 @@ int filter_impl(const Image& im, int r, long rank, unsigned flags, int drop_bits
     HistJob job;
     rc = make_hist_job(im, r, K, flags, drop_bits, p, desc, ws->err, &job);
     if (rc) return rc;
-    if (hist_smem_bytes(32 * p.ppl, r, p.nslots, p.cw) > (size_t)di.smem_optin)
+    if (plan_smem(p, r) > (size_t)di.smem_optin)
         return fail(HRM_ENOTSUP, "plan needs more shared memory than the device offers");
     e = launch_hist(job, st);
     return e == cudaSuccess ? HRM_OK : cuda_fail(e, "hist launch");
@@ -375,7 +389,7 @@ int hrm_get_plan(int dtype, int dims, int width, int height, int depth, int radi
     PlanH p = resolve_plan(dtype, dims, width, height, depth, radius, flags, di, nullptr);
     plan->tile_width = 32 * p.ppl;
     plan->strip_height = p.sh;
-    plan->slot_kbytes = (int)((hist_smem_bytes(32 * p.ppl, radius, p.nslots, p.cw) + 1023) / 1024);
+    plan->slot_kbytes = (int)((plan_smem(p, radius) + 1023) / 1024);
     plan->path = p.path;
     return HRM_OK;
 }

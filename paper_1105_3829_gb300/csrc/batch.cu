@@ -1,0 +1,424 @@
+// batch.cu -- many images / volumes of uneven size, dtype and radius in ONE
+// persistent kernel launch over a device tile work queue, plus its CUDA-graph
+// capture.
+//
+// Every job is cut into the same warp tiles its single-image launch would use
+// (hierarchical-histogram strips, or selection-network tiles for radius <= 2);
+// the tiles of all jobs form one queue.  A grid of resident warps repeatedly
+// takes the next tile with an atomic counter and runs the matching tile body,
+// so small and large jobs share the GPU without per-job launches or tails.
+// Outputs are bit-identical to the single-image calls: each tile computes
+// exactly what it computes there.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "runtime.h"
+#include "sortnet.cuh"
+
+namespace hrm {
+
+enum ItemKind : int { ITEM_HIST = 0, ITEM_SORT3 = 1, ITEM_SORT5 = 2 };
+
+struct BatchItem {
+    HistJob job;       // tile geometry, plan and rank (selection items use src/dst/pitches/W/H)
+    int kind;
+    int rows_per_warp; // selection-network tiles
+    int tiles_x_s;     // selection-network tiles across
+    int pad;
+};
+
+// Level pre-pass for many images at once (uniform trees need only the value range).
+struct LevelItem {
+    const unsigned char* src;
+    size_t sp, slice;
+    int W, H, D, elem;
+    LevelDesc* desc;
+    int mode;
+    int pad;
+};
+
+__global__ void batch_levels_init(const LevelItem* it, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    LevelDesc* d = it[j].desc;
+    d->mode = (uint32_t)it[j].mode;
+    d->vmin = 0xFFFFFFFFu;
+    d->vmax = 0;
+    d->count = 0;
+}
+
+__global__ void batch_minmax(const LevelItem* items, int n) {
+    const int j = blockIdx.y;
+    if (j >= n) return;
+    const LevelItem it = items[j];
+    uint32_t lo = 0xFFFFFFFFu, hi = 0;
+    const long rows = (long)it.H * it.D;
+    const int lane = threadIdx.x & 31;
+    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long nw = ((long)gridDim.x * blockDim.x) >> 5;
+    for (long row = warp; row < rows; row += nw) {
+        const int z = (int)(row / it.H), y = (int)(row % it.H);
+        const unsigned char* p = it.src + (size_t)z * it.slice + (size_t)y * it.sp;
+        for (int x = lane; x < it.W; x += 32) {
+            const uint32_t v = it.elem == 1 ? (uint32_t)__ldg(p + x)
+                                            : (uint32_t)__ldg(reinterpret_cast<const uint16_t*>(p) + x);
+            lo = min(lo, v);
+            hi = max(hi, v);
+        }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) {
+        atomicMin(&it.desc->vmin, lo);
+        atomicMax(&it.desc->vmax, hi);
+    }
+}
+
+__device__ void run_item(const BatchItem& it, int tile, unsigned char* sm) {
+    const HistJob& j = it.job;
+    if (it.kind != ITEM_HIST) {
+        const int tx = tile % it.tiles_x_s, ty = tile / it.tiles_x_s;
+        if (it.kind == ITEM_SORT3) {
+            if (j.elem == 1) sortnet3x3_tile<uint8_t>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);
+            else sortnet3x3_tile<uint16_t>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);
+        } else {
+            if (j.elem == 1) sortnet5x5_tile<uint8_t>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);
+            else sortnet5x5_tile<uint16_t>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);
+        }
+        return;
+    }
+#define HRM_CASE(T, P, C) \
+    if (j.ppl == P && j.cw == C) { hist_tile<T, P, C>(j, tile, sm); return; }
+    if (j.elem == 1) {
+        HRM_CASE(uint8_t, 2, 1) HRM_CASE(uint8_t, 4, 1) HRM_CASE(uint8_t, 8, 1)
+        HRM_CASE(uint8_t, 2, 2) HRM_CASE(uint8_t, 4, 2)
+    } else {
+        HRM_CASE(uint16_t, 2, 1) HRM_CASE(uint16_t, 4, 1) HRM_CASE(uint16_t, 8, 1)
+        HRM_CASE(uint16_t, 2, 2) HRM_CASE(uint16_t, 4, 2)
+    }
+#undef HRM_CASE
+    if ((threadIdx.x & 31) == 0) set_error(j.err, DEV_BAD_JOB);
+}
+
+__global__ void __launch_bounds__(32) batch_kernel(const BatchItem* __restrict__ items,
+                                                   const unsigned* __restrict__ tile_off, int nitems,
+                                                   unsigned* counter, unsigned total) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= total) break;
+        int lo = 0, hi = nitems - 1;  // last item whose first tile is <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const BatchItem it = items[lo];
+        run_item(it, (int)(t - tile_off[lo]), smem);
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+struct BatchDev {
+    BatchItem* items = nullptr;
+    unsigned* offs = nullptr;
+    LevelItem* litems = nullptr;
+    LevelDesc* descs = nullptr;
+    unsigned* counter = nullptr;
+    uint32_t* hist = nullptr;
+    unsigned* err = nullptr;
+    int cap = 0;
+    void* base = nullptr;
+};
+
+static int batchdev_alloc(BatchDev& b, int cap) {
+    const size_t bytes = sizeof(BatchItem) * cap + sizeof(unsigned) * (cap + 1) + sizeof(LevelItem) * cap +
+                         sizeof(LevelDesc) * cap + 256 + sizeof(uint32_t) * 2 * 4096 + 256;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes + 64 * 6);
+    if (e != cudaSuccess) return fail(HRM_ENOMEM, std::string("batch buffer cudaMalloc: ") + cudaGetErrorString(e));
+    auto align = [](unsigned char*& q) { q = (unsigned char*)(((uintptr_t)q + 63) & ~(uintptr_t)63); };
+    unsigned char* q = (unsigned char*)p;
+    b.base = p;
+    b.cap = cap;
+    align(q); b.items = (BatchItem*)q; q += sizeof(BatchItem) * cap;
+    align(q); b.offs = (unsigned*)q; q += sizeof(unsigned) * (cap + 1);
+    align(q); b.litems = (LevelItem*)q; q += sizeof(LevelItem) * cap;
+    align(q); b.descs = (LevelDesc*)q; q += sizeof(LevelDesc) * cap;
+    align(q); b.counter = (unsigned*)q; q += 128;
+    b.err = (unsigned*)q; q += 128;
+    align(q); b.hist = (uint32_t*)q;
+    e = cudaMemset(p, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "batch buffer memset");
+    return HRM_OK;
+}
+
+static void batchdev_free(BatchDev& b) {
+    if (b.base) cudaFree(b.base);
+    b = BatchDev{};
+}
+
+// Host-side plan of a batch: items in queue order plus the pre-pass list.
+struct BatchPlan {
+    std::vector<BatchItem> items;
+    std::vector<unsigned> offs;
+    std::vector<LevelItem> levels;      // uniform pre-pass items
+    std::vector<int> adaptive;          // indices into levels that need the adaptive pre-pass
+    std::vector<Image> copies;          // radius-0 jobs
+    size_t smem = 0;
+    unsigned total = 0;
+};
+
+static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, BatchPlan& bp) {
+    const DeviceInfo& di = device_info();
+    struct Tmp { BatchItem it; double cost; };
+    std::vector<Tmp> tmp;
+    for (int i = 0; i < njobs; ++i) {
+        const hrm_job& jb = jobs[i];
+        if (jb.dims != 2 && jb.dims != 3) return fail(HRM_EINVAL, "job dims must be 2 or 3");
+        Image im{jb.dtype, jb.dims, jb.src, jb.dst, jb.src_pitch, jb.src_slice_pitch, jb.dst_pitch,
+                 jb.dst_slice_pitch, jb.width, jb.height, jb.dims == 3 ? jb.depth : 1};
+        int rc = validate(im, jb.radius, HRM_BORDER_REPLICATE, jb.flags);
+        if (rc) return fail(rc, "job " + std::to_string(i) + ": " + hrm_last_error());
+        if (im.W == 0 || im.H == 0 || im.D == 0) continue;
+        const long n = 2L * jb.radius + 1, N = jb.dims == 3 ? n * n * n : n * n;
+        if (jb.rank < -1 || jb.rank >= N) return fail(HRM_EINVAL, "job " + std::to_string(i) + ": rank out of range");
+        if (jb.radius == 0) {
+            bp.copies.push_back(im);
+            continue;
+        }
+        const bool median = jb.rank < 0 || jb.rank == (N - 1) / 2;
+        const uint32_t K = (uint32_t)(jb.rank < 0 ? (N + 1) / 2 : jb.rank + 1);
+        const PlanH p = resolve_plan(jb.dtype, jb.dims, im.W, im.H, im.D, jb.radius, jb.flags, di, nullptr);
+        Tmp t{};
+        const int es = jb.dtype == HRM_U16 ? 2 : 1;
+        if (jb.dims == 2 && p.path == 1 && jb.radius <= 2 && median) {
+            t.it.kind = jb.radius == 1 ? ITEM_SORT3 : ITEM_SORT5;
+            t.it.rows_per_warp = 32;
+            t.it.tiles_x_s = (im.W + 255) / 256;
+            HistJob& h = t.it.job;
+            h.src = (const unsigned char*)im.src;
+            h.dst = (unsigned char*)im.dst;
+            h.s_row = im.sp;
+            h.d_row = im.dp;
+            h.W = im.W;
+            h.H = im.H;
+            h.elem = es;
+            h.ntiles = t.it.tiles_x_s * ((im.H + 31) / 32);
+            t.cost = 1.0;
+        } else {
+            const LevelDesc* desc = nullptr;
+            if (es == 2 || (jb.flags & HRM_ADAPTIVE)) {
+                const int li = (int)bp.levels.size();
+                if (li >= dev.cap) return fail(HRM_ENOTSUP, "too many jobs for the batch buffer");
+                LevelItem L{(const unsigned char*)im.src, im.sp, im.dims == 3 ? im.sslice : 0, im.W, im.H,
+                            im.D, es, dev.descs + li, (jb.flags & HRM_ADAPTIVE) ? 1 : 0, 0};
+                bp.levels.push_back(L);
+                if (jb.flags & HRM_ADAPTIVE) bp.adaptive.push_back(li);
+                desc = dev.descs + li;
+            }
+            t.it.kind = ITEM_HIST;
+            rc = make_hist_job(im, jb.radius, K, jb.flags, 0, p, desc, dev.err, &t.it.job);
+            if (rc) return rc;
+            bp.smem = std::max(bp.smem, plan_smem(p, jb.radius));
+            // expensive tiles first: work per tile grows with the strip and the window
+            t.cost = (double)p.sh * (32.0 * p.ppl + 2.0 * jb.radius) * (jb.dims == 3 ? n : 1);
+        }
+        tmp.push_back(t);
+    }
+    std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp& a, const Tmp& b) { return a.cost > b.cost; });
+    if ((int)tmp.size() > dev.cap) return fail(HRM_ENOTSUP, "too many jobs for the batch buffer");
+    unsigned off = 0;
+    for (auto& t : tmp) {
+        bp.items.push_back(t.it);
+        bp.offs.push_back(off);
+        off += (unsigned)t.it.job.ntiles;
+    }
+    bp.offs.push_back(off);
+    bp.total = off;
+    return HRM_OK;
+}
+
+cudaError_t launch_levels_adaptive_only(int elem, const void* src, size_t sp, size_t slice, int W, int H,
+                                        int D, LevelDesc* desc, uint32_t* hist, int num_sms, cudaStream_t st);
+
+// Enqueue a planned batch whose tables are already on the device.
+static int enqueue_batch(const BatchPlan& bp, const BatchDev& dev, cudaStream_t st) {
+    const DeviceInfo& di = device_info();
+    cudaError_t e;
+    for (const Image& im : bp.copies) {
+        const size_t es = im.dtype == HRM_U16 ? 2 : 1;
+        for (int z = 0; z < im.D; ++z) {
+            e = cudaMemcpy2DAsync((unsigned char*)im.dst + z * im.dslice, im.dp,
+                                  (const unsigned char*)im.src + z * im.sslice, im.sp, im.W * es, im.H,
+                                  cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "batch copy");
+        }
+    }
+    if (bp.total == 0) return HRM_OK;
+    const int nl = (int)bp.levels.size();
+    if (nl > 0) {
+        batch_levels_init<<<(nl + 127) / 128, 128, 0, st>>>(dev.litems, nl);
+        dim3 g(std::max(1, std::min(64, di.num_sms * 8 / std::max(1, nl))), nl);
+        batch_minmax<<<g, 256, 0, st>>>(dev.litems, nl);
+        for (int li : bp.adaptive) {
+            const LevelItem& L = bp.levels[li];
+            e = launch_levels_adaptive_only(L.elem, L.src, L.sp, L.slice, L.W, L.H, L.D, L.desc, dev.hist,
+                                            di.num_sms, st);
+            if (e != cudaSuccess) return cuda_fail(e, "adaptive pre-pass");
+        }
+    }
+    e = cudaMemsetAsync(dev.counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch counter reset");
+    const size_t smem = bp.smem;
+    if (smem > (size_t)di.smem_optin) return fail(HRM_ENOTSUP, "batch plan exceeds shared memory");
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, "batch smem attribute");
+    }
+    int per_sm = std::max(1, std::min(di.max_blocks_per_sm, (int)(di.smem_per_sm / (smem + 1024))));
+    unsigned grid = (unsigned)std::min<long>((long)di.num_sms * per_sm, (long)bp.total);
+    batch_kernel<<<grid, 32, smem, st>>>(dev.items, dev.offs, (int)bp.items.size(), dev.counter, bp.total);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? HRM_OK : cuda_fail(e, "batch kernel launch");
+}
+
+static int upload_plan(const BatchPlan& bp, const BatchDev& dev, cudaStream_t st, bool sync) {
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void* d, const void* h, size_t n) {
+        if (!n || e != cudaSuccess) return;
+        e = sync ? cudaMemcpy(d, h, n, cudaMemcpyHostToDevice) : cudaMemcpyAsync(d, h, n, cudaMemcpyHostToDevice, st);
+    };
+    cp(dev.items, bp.items.data(), sizeof(BatchItem) * bp.items.size());
+    cp(dev.offs, bp.offs.data(), sizeof(unsigned) * bp.offs.size());
+    cp(dev.litems, bp.levels.data(), sizeof(LevelItem) * bp.levels.size());
+    return e == cudaSuccess ? HRM_OK : cuda_fail(e, "batch table upload");
+}
+
+// Per-(device, stream) batch buffers for hrm_filter_batch.
+static std::mutex g_bmu;
+static std::vector<std::pair<std::pair<int, cudaStream_t>, BatchDev>> g_bufs;
+
+static int batch_buffers(cudaStream_t st, int need, BatchDev** out) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_bmu);
+    for (auto& kv : g_bufs)
+        if (kv.first.first == dev && kv.first.second == st) {
+            if (kv.second.cap < need) {
+                cudaStreamSynchronize(st);  // the old tables may still be in use
+                batchdev_free(kv.second);
+                int rc = batchdev_alloc(kv.second, std::max(need, 256));
+                if (rc) return rc;
+            }
+            *out = &kv.second;
+            return HRM_OK;
+        }
+    g_bufs.push_back({{dev, st}, BatchDev{}});
+    int rc = batchdev_alloc(g_bufs.back().second, std::max(need, 256));
+    if (rc) return rc;
+    *out = &g_bufs.back().second;
+    return HRM_OK;
+}
+
+}  // namespace hrm
+
+using namespace hrm;
+
+struct hrm_batch_graph {
+    BatchDev dev;
+    BatchPlan plan;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+int hrm_filter_batch(const hrm_job* jobs, int njobs, void* stream) {
+    if (njobs < 0 || (njobs > 0 && !jobs)) return fail(HRM_EINVAL, "bad job list");
+    if (njobs == 0) return HRM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    BatchDev* dev = nullptr;
+    int rc = batch_buffers(st, njobs, &dev);
+    if (rc) return rc;
+    Workspace* ws = nullptr;
+    rc = workspace_for(st, &ws);
+    if (rc) return rc;
+    dev->err = ws->err;  // kernel error flags surface through hrm_device_status(stream)
+    BatchPlan bp;
+    rc = plan_batch(jobs, njobs, *dev, bp);
+    if (rc) return rc;
+    rc = upload_plan(bp, *dev, st, false);
+    if (rc) return rc;
+    return enqueue_batch(bp, *dev, st);
+}
+
+int hrm_batch_graph_create(const hrm_job* jobs, int njobs, void* stream, hrm_batch_graph** out) {
+    if (!out || njobs <= 0 || !jobs) return fail(HRM_EINVAL, "bad job list");
+    (void)stream;
+    auto* g = new hrm_batch_graph();
+    int rc = batchdev_alloc(g->dev, std::max(njobs, 1));
+    if (rc) { delete g; return rc; }
+    rc = plan_batch(jobs, njobs, g->dev, g->plan);
+    if (!rc) rc = upload_plan(g->plan, g->dev, nullptr, true);
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) rc = cuda_fail(e, "capture stream");
+    }
+    if (!rc) {
+        // configure kernel attributes before capture (not stream operations)
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamBeginCapture");
+        else {
+            rc = enqueue_batch(g->plan, g->dev, cs);
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamEndCapture(cs, &graph);
+            if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamEndCapture");
+            g->graph = graph;
+            if (!rc) {
+                e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+                if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate");
+            }
+        }
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (rc) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        batchdev_free(g->dev);
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return HRM_OK;
+}
+
+int hrm_batch_graph_launch(hrm_batch_graph* g, void* stream) {
+    if (!g || !g->exec) return fail(HRM_EINVAL, "null graph");
+    cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? HRM_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+int hrm_batch_graph_destroy(hrm_batch_graph* g) {
+    if (!g) return HRM_OK;
+    cudaDeviceSynchronize();
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    batchdev_free(g->dev);
+    delete g;
+    return HRM_OK;
+}
+
+}  // extern "C"

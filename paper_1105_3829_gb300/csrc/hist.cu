@@ -41,7 +41,7 @@ static cudaError_t launch_t(const HistJob& job, size_t smem, cudaStream_t st) {
 }
 
 cudaError_t launch_hist(const HistJob& job, cudaStream_t st) {
-    const size_t smem = hist_smem_bytes(32 * job.ppl, job.r, job.nslots, job.cw);
+    const size_t smem = hist_smem_bytes(32 * job.ppl, job.r, job.nslots, job.cw, job.ring, job.elem);
     return job.elem == 1 ? launch_t<uint8_t>(job, smem, st) : launch_t<uint16_t>(job, smem, st);
 }
 

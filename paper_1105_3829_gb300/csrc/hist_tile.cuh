@@ -59,12 +59,20 @@ struct HistJob {
     int elem;                // 1 or 2 bytes per value
     int ppl;                 // pixels per lane
     int cw;                  // counter width in bytes (1 or 2)
+    int ring;                // 2D only: stage the last n+1 input rows in shared memory
     unsigned* err;           // device error word (may be null)
 };
 
-__host__ __device__ inline size_t hist_smem_bytes(int tw, int r, int nslots, int cw) {
+// Ring of the last n+1 input rows (2D): (n+1) rows x NC columns, padded to 16 bytes.
+__host__ __device__ inline size_t hist_ring_bytes(int tw, int r, int elem) {
+    size_t b = (size_t)(2 * r + 2) * (size_t)(tw + 2 * r) * elem;
+    return (b + 15) & ~(size_t)15;
+}
+
+__host__ __device__ inline size_t hist_smem_bytes(int tw, int r, int nslots, int cw, int ring = 0, int elem = 2) {
     int nc = tw + 2 * r;
-    return (size_t)META_BYTES + (size_t)(nc + 1) * 32 + (size_t)nslots * nc * 16 * cw;
+    return (size_t)META_BYTES + (size_t)(nc + 1) * 32 + (size_t)nslots * nc * 16 * cw +
+           (ring ? hist_ring_bytes(tw, r, elem) : 0);
 }
 
 // ---- counter records (16 bins, CW bytes per bin) ---------------------------------
@@ -133,10 +141,15 @@ __device__ __forceinline__ uint32_t geo_ld(const Geo& g, int t, int i, int gx) {
     return (uint32_t)__ldg(reinterpret_cast<const T*>(g.src + (size_t)tc * g.tstride + (size_t)ic * g.istride) + gx);
 }
 
-// Build slot s for node `key` at walk position t from the staged values of every column.
+__device__ __forceinline__ int ring_idx(int u, int M) { return (u + M) % M; }
+
+// Build slot s for node `key` at walk position t from the staged values of
+// every column: from the shared-memory ring of the last n+1 rows when present
+// (2D), else from global memory with the lane's columns interleaved so that
+// several independent loads are in flight.
 template <typename T, int CW>
 __device__ void build_slot(const HistJob& a, const Geo& g, const Meta& m, unsigned char* slots, int NC,
-                           int x0, int t, int s, uint32_t key) {
+                           int x0, int t, int s, uint32_t key, const T* ring) {
     const int lane = threadIdx.x & 31;
     const int r = a.r;
     const int level = (int)(key >> 20);
@@ -151,24 +164,49 @@ __device__ void build_slot(const HistJob& a, const Geo& g, const Meta& m, unsign
         hi = min(lo + (1u << top), m.e[c + 1]);
         dshift = top - b;
     }
-    for (int cx = lane; cx < NC; cx += 32) {
-        const int gx = clampi(x0 - r + cx, 0, a.W - 1);
-        uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int tt = t - r; tt <= t + r; ++tt) {
+    auto digit = [&](uint32_t v) -> int {
+        if (level == 0) return coarse_of(m, v);
+        if (v < lo || v >= hi) return -1;
+        return (int)((v - lo) >> dshift);
+    };
+    if (ring) {
+        const int M = 2 * r + 2;
+        for (int cx = lane; cx < NC; cx += 32) {
+            uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll 4
+            for (int tt = t - r; tt <= t + r; ++tt) {
+                const int d = digit((uint32_t)ring[(size_t)ring_idx(tt, M) * NC + cx]);
+                if (d >= 0) reg_count<CW>(cnt, d);
+            }
+            rec_store<CW>(slots + ((size_t)s * NC + cx) * 16 * CW, cnt);
+        }
+        return;
+    }
+    // global: process the lane's columns four at a time
+    for (int cb = lane; cb < NC; cb += 128) {
+        uint32_t cnt[4][8];
+        int gx[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) cnt[j][k] = 0;
+            gx[j] = clampi(x0 - r + cb + 32 * j, 0, a.W - 1);
+        }
+        for (int tt = t - r; tt <= t + r; ++tt) {
             for (int i = 0; i < g.layer; ++i) {
-                const uint32_t v = geo_ld<T>(g, tt, i, gx);
-                int d;
-                if (level == 0) {
-                    d = coarse_of(m, v);
-                } else {
-                    if (v < lo || v >= hi) continue;
-                    d = (int)((v - lo) >> dshift);
+                uint32_t v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[j] = geo_ld<T>(g, tt, i, gx[j]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int d = digit(v[j]);
+                    if (d >= 0) reg_count<CW>(cnt[j], d);
                 }
-                reg_count<CW>(cnt, d);
             }
         }
-        rec_store<CW>(slots + ((size_t)s * NC + cx) * 16 * CW, cnt);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (cb + 32 * j < NC) rec_store<CW>(slots + ((size_t)s * NC + cb + 32 * j) * 16 * CW, cnt[j]);
     }
 }
 
@@ -198,7 +236,9 @@ __device__ __forceinline__ void slot_prefix(const unsigned char* slots, uint4* p
                                             int lo, int hi) {
     const int lane = threadIdx.x & 31;
     const int mcols = hi - lo + 1;
-    const int q = (mcols + 31) >> 5;
+    // Odd chunk length: lanes read columns q records apart, and an odd q spreads
+    // the 16-byte records of a quarter-warp over distinct bank groups.
+    const int q = ((mcols + 31) >> 5) | 1;
     const int c_begin = lo + lane * q;
     const int c_end = min(c_begin + q, hi + 1);
     uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -282,6 +322,11 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     Meta& m = *reinterpret_cast<Meta*>(sm);
     uint4* pfx = reinterpret_cast<uint4*>(sm + META_BYTES);
     unsigned char* slots = sm + META_BYTES + (size_t)(NC + 1) * 32;
+    const bool use_ring = a.ring && a.dims == 2;
+    T* ring = use_ring ? reinterpret_cast<T*>(slots + (size_t)S * NC * 16 * CW) : nullptr;
+    const int M = 2 * r + 2;  // ring rows
+    // the lane's columns cx = lane + 32*j, j < CPL, cover NC <= 32*PPL + 2*127
+    constexpr int CPL = PPL + 8;
 
     load_levels(m, a.desc, a.fixed_shift);
     if (lane < MAX_SLOTS) {
@@ -291,8 +336,40 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     }
     __syncwarp();
     rehash(m, S);
-    build_slot<T, CW>(a, g, m, slots, NC, x0, ts, 0, 0u);
+    if (use_ring) {  // stage input rows ts-r-1 .. ts+r
+        for (int u = ts - r - 1; u <= ts + r; ++u) {
+            const T* row = reinterpret_cast<const T*>(a.src + (size_t)clampi(u, 0, L - 1) * a.s_row);
+            T* dst = ring + (size_t)ring_idx(u, M) * NC;
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                const int cx = lane + 32 * j;
+                if (cx < NC) dst[cx] = __ldg(row + clampi(x0 - r + cx, 0, a.W - 1));
+            }
+        }
+        __syncwarp();
+    }
+    build_slot<T, CW>(a, g, m, slots, NC, x0, ts, 0, 0u, ring);
     __syncwarp();
+
+    // 2D: the entering (and, without the ring, the leaving) values of the next
+    // step are loaded one step ahead, so their latency hides behind the walk.
+    uint32_t nin[CPL], nout[CPL];
+    auto prefetch = [&](int tn) {
+        if (a.dims != 2 || tn >= te) return;
+        const int ti = clampi(tn + r, 0, L - 1), to = clampi(tn - r - 1, 0, L - 1);
+        const T* rin = reinterpret_cast<const T*>(a.src + (size_t)ti * a.s_row);
+        const T* rout = reinterpret_cast<const T*>(a.src + (size_t)to * a.s_row);
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            const int cx = lane + 32 * j;
+            if (cx < NC) {
+                const int gx = clampi(x0 - r + cx, 0, a.W - 1);
+                nin[j] = __ldg(rin + gx);
+                if (!use_ring) nout[j] = __ldg(rout + gx);
+            }
+        }
+    };
+    prefetch(ts + 1);
 
     // cost model in warp instructions: one shared prefix vs direct n-column sums
     const int prefix_cost = ((NC + 31) >> 5) * (CW == 1 ? 31 : 24) + 120;
@@ -304,20 +381,44 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         if (t > ts) {
             const int to = clampi(t - r - 1, 0, L - 1);
             const int ti = clampi(t + r, 0, L - 1);
-            if (to != ti) {
-                for (int cx = lane; cx < NC; cx += 32) {
-                    const int gx = clampi(x0 - r + cx, 0, a.W - 1);
-                    for (int i = 0; i < g.layer; ++i) {
-                        const uint32_t vo = geo_ld<T>(g, to, i, gx);
-                        const uint32_t vi = geo_ld<T>(g, ti, i, gx);
+            if (a.dims == 2) {
+                T* rin = use_ring ? ring + (size_t)ring_idx(t + r, M) * NC : nullptr;
+                const T* rout = use_ring ? ring + (size_t)ring_idx(t - r - 1, M) * NC : nullptr;
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) {
+                    const int cx = lane + 32 * j;
+                    if (cx < NC) {
+                        const uint32_t vi = nin[j];
+                        const uint32_t vo = use_ring ? (uint32_t)rout[cx] : nout[j];
+                        if (use_ring) rin[cx] = (T)vi;
                         if (vo != vi) {
                             column_update<CW>(m, slots, NC, cx, vo, -1);
                             column_update<CW>(m, slots, NC, cx, vi, +1);
                         }
                     }
                 }
+            } else if (to != ti) {
+                for (int cx = lane; cx < NC; cx += 32) {
+                    const int gx = clampi(x0 - r + cx, 0, a.W - 1);
+                    for (int i = 0; i < g.layer; i += 4) {
+                        uint32_t vo[4], vi[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int ii = min(i + k, g.layer - 1);
+                            vo[k] = geo_ld<T>(g, to, ii, gx);
+                            vi[k] = geo_ld<T>(g, ti, ii, gx);
+                        }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (i + k < g.layer && vo[k] != vi[k]) {
+                                column_update<CW>(m, slots, NC, cx, vo[k], -1);
+                                column_update<CW>(m, slots, NC, cx, vi[k], +1);
+                            }
+                    }
+                }
             }
             __syncwarp();
+            prefetch(t + 1);
         }
 
         // ---- level walk for the TW outputs at walk position t ----
@@ -396,7 +497,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                     }
                     __syncwarp();
                     rehash(m, S);
-                    build_slot<T, CW>(a, g, m, slots, NC, x0, t, victim, nk);
+                    build_slot<T, CW>(a, g, m, slots, NC, x0, t, victim, nk, ring);
 #pragma unroll
                     for (int k = 0; k < PPL; ++k)
                         if (todo[k] && slot[k] < 0 && key[k] == nk) slot[k] = victim;

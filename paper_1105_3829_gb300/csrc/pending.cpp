@@ -2,10 +2,6 @@
 #include "../../include/hrm.h"
 
 extern "C" {
-int hrm_filter_batch(const hrm_job*, int, void*) { return HRM_ENOTSUP; }
-int hrm_batch_graph_create(const hrm_job*, int, void*, hrm_batch_graph**) { return HRM_ENOTSUP; }
-int hrm_batch_graph_launch(hrm_batch_graph*, void*) { return HRM_ENOTSUP; }
-int hrm_batch_graph_destroy(hrm_batch_graph*) { return HRM_ENOTSUP; }
 int hrm_autotune(int, int, int, int, int, int, unsigned, void*, hrm_plan*) { return HRM_ENOTSUP; }
 int hrm_server_create(void*, size_t, int, int, hrm_server**) { return HRM_ENOTSUP; }
 int hrm_submit(hrm_server*, const hrm_request*, uint64_t*) { return HRM_ENOTSUP; }

@@ -203,3 +203,24 @@ cudaError_t launch_levels(int elem, bool adaptive, const void* src, size_t sp, s
 }
 
 }  // namespace hrm
+
+namespace hrm {
+
+// Adaptive boundaries for a descriptor whose value range is already known
+// (the batched pre-pass computes the ranges of all jobs in one launch).
+cudaError_t launch_levels_adaptive_only(int elem, const void* src, size_t sp, size_t slice, int W, int H,
+                                        int D, LevelDesc* desc, uint32_t* hist, int num_sms,
+                                        cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 2 * PREHIST_BINS, st);
+    if (e != cudaSuccess) return e;
+    auto s = (const unsigned char*)src;
+    long nblk = (long)((W + 7) / 8) * ((H + 7) / 8) * D;
+    int hb = (int)std::min<long>((nblk + 255) / 256, (long)num_sms * 2);
+    if (hb < 1) hb = 1;
+    if (elem == 1) prehist_kernel<uint8_t><<<hb, 256, 0, st>>>(s, sp, slice, W, H, D, desc, hist);
+    else prehist_kernel<uint16_t><<<hb, 256, 0, st>>>(s, sp, slice, W, H, D, desc, hist);
+    edges_kernel<<<1, 1024, 0, st>>>(desc, hist);
+    return cudaGetLastError();
+}
+
+}  // namespace hrm

@@ -44,6 +44,8 @@ struct PlanH {
     int nslots;   // slots per warp incl. root
     int path;     // 1 = selection network, 2 = histogram
     int cw;       // counter width (bytes)
+    int ring;     // stage the last n+1 input rows in shared memory (2D)
+    int es;       // element size (bytes)
 };
 struct ProblemKey {
     int dtype, dims, width, height, depth, radius;
@@ -52,10 +54,11 @@ struct ProblemKey {
 bool plan_lookup(const ProblemKey& k, hrm_plan* p);
 void plan_store(const ProblemKey& k, const hrm_plan& p);
 // dims 2: lines = 1, walk = H; dims 3: lines = H (one tile row per y), walk = D.
-PlanH default_plan(int dims, int W, int lines, int walk, int r, const DeviceInfo& di);
+PlanH default_plan(int dims, int es, int W, int lines, int walk, int r, const DeviceInfo& di);
 PlanH resolve_plan(int dtype, int dims, int W, int H, int D, int r, unsigned flags, const DeviceInfo& di,
                    const hrm_plan* force);
 int slots_for(int tw, int r, int cw, size_t budget);
+size_t plan_smem(const PlanH& p, int r);
 int counter_width(int dims, int r);
 
 // Kernel launchers (defined in the .cu files).

@@ -1,0 +1,312 @@
+// sortnet.cuh -- exact median for radius 1 and 2 (3x3, 5x5) by register
+// selection networks.
+//
+// For windows this small the paper itself notes that direct selection is
+// competitive (Section IV: Quickselect loses to the tree method only for
+// windows larger than 4x4).  On the GPU the direct form is a fixed network of
+// min/max operations in registers:
+//   * every lane owns 8 consecutive columns and slides down a run of rows;
+//   * each column's vertical n-tuple is sorted once and shared by the n
+//     horizontally neighbouring outputs (neighbour lanes exchange their edge
+//     columns with warp shuffles);
+//   * two adjacent columns travel together as a packed uint16 pair, so every
+//     min/max (native min.u16x2 / max.u16x2) serves two outputs.
+// r = 1: median of 9 from three sorted columns is
+//        med3(max of the lows, med3 of the middles, min of the highs).
+// r = 2: the 5x5 block with sorted columns is row-sorted, 12 of its entries
+//        are provably off-median, and the 7th smallest of the remaining 13 is
+//        the median; the networks are Batcher odd-even merge sorts generated
+//        at compile time and pruned to the outputs actually used.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hrm_common.cuh"
+
+namespace hrm {
+
+// ---------------------------------------------------------------------------
+// Compile-time Batcher odd-even merge sort comparator lists for n <= 32
+// (generated for the next power of two; comparators touching an index >= n
+// are dropped, which is the same as padding with +infinity).
+struct Net {
+    int n = 0;
+    unsigned char a[256] = {};
+    unsigned char b[256] = {};
+};
+
+constexpr Net make_net(int N) {
+    Net net{};
+    int P = 1;
+    while (P < N) P <<= 1;
+    for (int p = 1; p < P; p <<= 1)
+        for (int k = p; k >= 1; k >>= 1)
+            for (int j = k % p; j + k < P; j += 2 * k)
+                for (int i = 0; i < k; ++i)
+                    if ((i + j) / (2 * p) == (i + j + k) / (2 * p)) {
+                        int lo = i + j, hi = i + j + k;
+                        if (hi < N) {
+                            net.a[net.n] = (unsigned char)lo;
+                            net.b[net.n] = (unsigned char)hi;
+                            ++net.n;
+                        }
+                    }
+    return net;
+}
+
+template <int N>
+struct NetOf {
+    static constexpr Net net = make_net(N);
+};
+
+// Sort v[0..N) ascending (per 16-bit half) with the Batcher network.
+template <int N>
+__device__ __forceinline__ void sortnet(uint32_t (&v)[N]) {
+    constexpr Net net = NetOf<N>::net;
+#pragma unroll
+    for (int c = 0; c < net.n; ++c) {
+        const int i = net.a[c], j = net.b[c];
+        uint32_t lo = vmin2(v[i], v[j]);
+        uint32_t hi = vmax2(v[i], v[j]);
+        v[i] = lo;
+        v[j] = hi;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row loads: 8 consecutive columns starting at x as 4 packed uint16 pairs.
+template <typename T>
+__device__ __forceinline__ void load8(const unsigned char* src, size_t sp, int W, int y, int x,
+                                      uint32_t (&p)[4]) {
+    const unsigned char* row = src + (size_t)y * sp;
+    if (x + 7 < W) {
+        const T* ptr = reinterpret_cast<const T*>(row) + x;
+        if (sizeof(T) == 2 && (reinterpret_cast<uintptr_t>(ptr) & 15) == 0) {
+            uint4 q = __ldg(reinterpret_cast<const uint4*>(ptr));
+            p[0] = q.x; p[1] = q.y; p[2] = q.z; p[3] = q.w;
+            return;
+        }
+        if (sizeof(T) == 1 && (reinterpret_cast<uintptr_t>(ptr) & 7) == 0) {
+            uint2 q = __ldg(reinterpret_cast<const uint2*>(ptr));
+            p[0] = lo_pair(q.x); p[1] = hi_pair(q.x);
+            p[2] = lo_pair(q.y); p[3] = hi_pair(q.y);
+            return;
+        }
+    }
+    const T* r = reinterpret_cast<const T*>(row);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t a = __ldg(r + min(x + 2 * k, W - 1));
+        uint32_t b = __ldg(r + min(x + 2 * k + 1, W - 1));
+        p[k] = a | (b << 16);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t load1(const unsigned char* src, size_t sp, int W, int y, int x) {
+    x = clampi(x, 0, W - 1);
+    return (uint32_t)__ldg(reinterpret_cast<const T*>(src + (size_t)y * sp) + x);
+}
+
+template <typename T>
+__device__ __forceinline__ void store8(unsigned char* dst, size_t dp, int W, int y, int x,
+                                       const uint32_t (&o)[4]) {
+    unsigned char* row = dst + (size_t)y * dp;
+    if (x + 7 < W) {
+        T* ptr = reinterpret_cast<T*>(row) + x;
+        if (sizeof(T) == 2 && (reinterpret_cast<uintptr_t>(ptr) & 15) == 0) {
+            *reinterpret_cast<uint4*>(ptr) = make_uint4(o[0], o[1], o[2], o[3]);
+            return;
+        }
+        if (sizeof(T) == 1 && (reinterpret_cast<uintptr_t>(ptr) & 7) == 0) {
+            *reinterpret_cast<uint2*>(ptr) =
+                make_uint2(__byte_perm(o[0], o[1], 0x6420), __byte_perm(o[2], o[3], 0x6420));
+            return;
+        }
+    }
+    T* r = reinterpret_cast<T*>(row);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (x + 2 * k < W) r[x + 2 * k] = (T)(o[k] & 0xFFFFu);
+        if (x + 2 * k + 1 < W) r[x + 2 * k + 1] = (T)(o[k] >> 16);
+    }
+}
+
+// (hi half of a, lo half of b): the pair shifted by one column.
+__device__ __forceinline__ uint32_t shift1(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x5432); }
+
+__device__ __forceinline__ uint32_t med3(uint32_t a, uint32_t b, uint32_t c) {
+    return vmax2(vmin2(a, b), vmin2(vmax2(a, b), c));
+}
+
+// ---------------------------------------------------------------------------
+// r = 1
+// One warp: 256 columns starting at tile_x*256, rows [tile_y*rpw, +rpw).
+template <typename T>
+__device__ void sortnet3x3_tile(const unsigned char* __restrict__ src, size_t sp,
+                                unsigned char* __restrict__ dst, size_t dp, int W, int H,
+                                int rows_per_warp, int tile_x, int tile_y) {
+    const int lane = threadIdx.x & 31;
+    const int x = tile_x * 256 + lane * 8;
+    const int y0 = tile_y * rows_per_warp;
+    if (y0 >= H || tile_x * 256 >= W) return;
+    const int y1 = min(y0 + rows_per_warp, H);
+
+    uint32_t a[4], b[4], c[4];
+    uint32_t ea, eb, ec;  // halo column (lane 0: x-1, lane 31: x+8), duplicated in both halves
+    const int hx = lane == 0 ? x - 1 : x + 8;
+    load8<T>(src, sp, W, clampi(y0 - 1, 0, H - 1), x, a);
+    load8<T>(src, sp, W, y0, x, b);
+    ea = load1<T>(src, sp, W, clampi(y0 - 1, 0, H - 1), hx) * 0x10001u;
+    eb = load1<T>(src, sp, W, y0, hx) * 0x10001u;
+    for (int y = y0; y < y1; ++y) {
+        const int yn = min(y + 1, H - 1);
+        load8<T>(src, sp, W, yn, x, c);
+        ec = load1<T>(src, sp, W, yn, hx) * 0x10001u;
+        uint32_t lo[4], mi[4], hi[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t t1 = vmin2(a[k], b[k]), t2 = vmax2(a[k], b[k]);
+            lo[k] = vmin2(t1, c[k]);
+            uint32_t t3 = vmax2(t1, c[k]);
+            mi[k] = vmin2(t2, t3);
+            hi[k] = vmax2(t2, t3);
+        }
+        uint32_t elo, emi, ehi;
+        {
+            uint32_t t1 = vmin2(ea, eb), t2 = vmax2(ea, eb);
+            elo = vmin2(t1, ec);
+            uint32_t t3 = vmax2(t1, ec);
+            emi = vmin2(t2, t3);
+            ehi = vmax2(t2, t3);
+        }
+        // left neighbour pair (columns x-2, x-1) and right (x+8, x+9)
+        uint32_t llo = __shfl_up_sync(0xffffffffu, lo[3], 1);
+        uint32_t lmi = __shfl_up_sync(0xffffffffu, mi[3], 1);
+        uint32_t lhi = __shfl_up_sync(0xffffffffu, hi[3], 1);
+        uint32_t rlo = __shfl_down_sync(0xffffffffu, lo[0], 1);
+        uint32_t rmi = __shfl_down_sync(0xffffffffu, mi[0], 1);
+        uint32_t rhi = __shfl_down_sync(0xffffffffu, hi[0], 1);
+        if (lane == 0) { llo = elo; lmi = emi; lhi = ehi; }
+        if (lane == 31) { rlo = elo; rmi = emi; rhi = ehi; }
+        uint32_t o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t plo = k == 0 ? llo : lo[k - 1], pmi = k == 0 ? lmi : mi[k - 1], phi = k == 0 ? lhi : hi[k - 1];
+            uint32_t nlo = k == 3 ? rlo : lo[k + 1], nmi = k == 3 ? rmi : mi[k + 1], nhi = k == 3 ? rhi : hi[k + 1];
+            uint32_t Llo = shift1(plo, lo[k]), Lmi = shift1(pmi, mi[k]), Lhi = shift1(phi, hi[k]);
+            uint32_t Rlo = shift1(lo[k], nlo), Rmi = shift1(mi[k], nmi), Rhi = shift1(hi[k], nhi);
+            uint32_t A = vmax2(vmax2(Llo, lo[k]), Rlo);
+            uint32_t B = med3(Lmi, mi[k], Rmi);
+            uint32_t C = vmin2(vmin2(Lhi, hi[k]), Rhi);
+            o[k] = med3(A, B, C);
+        }
+        store8<T>(dst, dp, W, y, x, o);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { a[k] = b[k]; b[k] = c[k]; }
+        ea = eb;
+        eb = ec;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// r = 2.  Positions (i = rank within a column, j = column after row sorting)
+// of the 5x5 block that can still hold the median: (i+1)(j+1) <= 13 and
+// (5-i)(5-j) <= 13.  Six entries are provably below it, so the median is the
+// 7th smallest (index 6) of these 13 candidates.
+__device__ __forceinline__ uint32_t median25_sorted_cols(uint32_t (&m)[5][5]) {
+    // m[j][i]: column j, rank i (columns already sorted ascending).
+    // Sort each rank-row across the five columns.
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        uint32_t r[5] = {m[0][i], m[1][i], m[2][i], m[3][i], m[4][i]};
+        sortnet<5>(r);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) m[j][i] = r[j];
+    }
+    uint32_t cand[13];
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+            if ((i + 1) * (j + 1) <= 13 && (5 - i) * (5 - j) <= 13) cand[q++] = m[j][i];
+    sortnet<13>(cand);
+    return cand[6];
+}
+
+template <typename T>
+__device__ void sortnet5x5_tile(const unsigned char* __restrict__ src, size_t sp,
+                                unsigned char* __restrict__ dst, size_t dp, int W, int H,
+                                int rows_per_warp, int tile_x, int tile_y) {
+    const int lane = threadIdx.x & 31;
+    const int x = tile_x * 256 + lane * 8;
+    const int y0 = tile_y * rows_per_warp;
+    if (y0 >= H || tile_x * 256 >= W) return;
+    const int y1 = min(y0 + rows_per_warp, H);
+
+    // rows y-2..y+2 of the lane's 8 columns, plus a halo pair: lane 0 holds
+    // columns (x-2, x-1), lane 31 holds (x+8, x+9).
+    uint32_t rw[5][4], he[5];
+    const int hx = lane == 0 ? x - 2 : x + 8;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        int yy = clampi(y0 - 2 + t, 0, H - 1);
+        load8<T>(src, sp, W, yy, x, rw[t]);
+        he[t] = load1<T>(src, sp, W, yy, hx) | (load1<T>(src, sp, W, yy, hx + 1) << 16);
+    }
+    for (int y = y0; y < y1; ++y) {
+        const int yn = min(y + 2, H - 1);
+        load8<T>(src, sp, W, yn, x, rw[4]);
+        he[4] = load1<T>(src, sp, W, yn, hx) | (load1<T>(src, sp, W, yn, hx + 1) << 16);
+        // sort each column pair vertically
+        uint32_t s[4][5], hs[5];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t v[5] = {rw[0][k], rw[1][k], rw[2][k], rw[3][k], rw[4][k]};
+            sortnet<5>(v);
+#pragma unroll
+            for (int t = 0; t < 5; ++t) s[k][t] = v[t];
+        }
+        {
+            uint32_t v[5] = {he[0], he[1], he[2], he[3], he[4]};
+            sortnet<5>(v);
+#pragma unroll
+            for (int t = 0; t < 5; ++t) hs[t] = v[t];
+        }
+        uint32_t lp[5], rp[5];  // pair (x-2, x-1) and (x+8, x+9) as sorted 5-tuples
+#pragma unroll
+        for (int t = 0; t < 5; ++t) {
+            lp[t] = __shfl_up_sync(0xffffffffu, s[3][t], 1);
+            rp[t] = __shfl_down_sync(0xffffffffu, s[0][t], 1);
+            if (lane == 0) lp[t] = hs[t];
+            if (lane == 31) rp[t] = hs[t];
+        }
+        uint32_t o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t m[5][5];
+#pragma unroll
+            for (int t = 0; t < 5; ++t) {
+                uint32_t P = k == 0 ? lp[t] : s[k - 1][t];  // columns 2k-2, 2k-1
+                uint32_t C = s[k][t];                        // 2k, 2k+1
+                uint32_t N = k == 3 ? rp[t] : s[k + 1][t];  // 2k+2, 2k+3
+                m[0][t] = P;
+                m[1][t] = shift1(P, C);
+                m[2][t] = C;
+                m[3][t] = shift1(C, N);
+                m[4][t] = N;
+            }
+            o[k] = median25_sorted_cols(m);
+        }
+        store8<T>(dst, dp, W, y, x, o);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) rw[t][k] = rw[t + 1][k];
+            he[t] = he[t + 1];
+        }
+    }
+}
+
+}  // namespace hrm
