@@ -156,22 +156,26 @@ int hrm_batch_graph_destroy(hrm_batch_graph* g);
 
 /* ---- planning / autotuning ---------------------------------------------
  *
- * The hierarchical kernels are parameterised by tile width (pixels per warp
- * row), strip height (rows walked per tile) and slot budget (shared memory
- * for cached histogram levels).  hrm_autotune times candidate plans for one
- * problem class on `stream` (it allocates and frees its own scratch images)
- * and caches the winner; later calls of the same class use it.  The cache is
- * per process; hrm_plan_save / hrm_plan_load persist it as a text file.
- * hrm_autotune blocks until the timing finishes. */
+ * The hierarchical kernels are parameterised by tile width (output columns
+ * per warp), strip length (rows or slices walked per tile) and the shared
+ * memory per warp for cached tree nodes.  hrm_autotune times candidate plans
+ * for one problem class on `stream` and caches the fastest; later calls of
+ * the same class (dtype, dims, size, radius, flags) use it.  The timing runs
+ * on `sample` (device pointer, the caller's pitches) when it is not NULL --
+ * speed depends on the data, so a representative image is best -- and on a
+ * synthetic image otherwise.  hrm_autotune allocates and frees its own output
+ * (and synthetic input) buffers and blocks until the timing finishes.  The
+ * cache is per process; hrm_plan_save / hrm_plan_load persist it as text. */
 typedef struct {
-    int tile_width;     /* output columns per warp tile (multiple of 32)     */
-    int strip_height;   /* output rows per tile                               */
-    int slot_kbytes;    /* shared memory per warp for histogram levels (KB)   */
+    int tile_width;     /* output columns per warp tile: 64, 128 or 256      */
+    int strip_height;   /* output rows (2D) or slices (3D) per tile           */
+    int slot_kbytes;    /* shared memory per warp for the tree nodes (KB)     */
     int path;           /* 0 = auto, 1 = selection network, 2 = histogram     */
 } hrm_plan;
 
 int hrm_autotune(int dtype, int dims, int width, int height, int depth, int radius,
-                 unsigned flags, void* stream, hrm_plan* best);
+                 unsigned flags, const void* sample, size_t sample_pitch,
+                 size_t sample_slice_pitch, void* stream, hrm_plan* best);
 int hrm_get_plan(int dtype, int dims, int width, int height, int depth, int radius,
                  unsigned flags, hrm_plan* plan);
 int hrm_set_plan(int dtype, int dims, int width, int height, int depth, int radius,

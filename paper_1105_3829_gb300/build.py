@@ -18,6 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libhrm.so")
+# Instrumented variant (per-phase device counters): _build/count/libhrm.so
+VARIANTS = {"count": ["-DHRM_COUNT_OPS"]}
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -40,15 +42,20 @@ def _deps() -> list[str]:
         glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def lib_path(variant: str | None = None) -> str:
+    return LIB if not variant else os.path.join(OUT, variant, "libhrm.so")
+
+
+def up_to_date(variant: str | None = None) -> bool:
+    lib = lib_path(variant)
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(OUT, os.path.basename(src) + ".o")
+def _compile(src: str, extra: list[str], out: str) -> str:
+    obj = os.path.join(out, os.path.basename(src) + ".o")
     cmd = [nvcc(), "-c", src, "-o", obj] + ARCH + CFLAGS + extra
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -58,25 +65,29 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(force: bool = False, extra: list[str] | None = None, jobs: int | None = None) -> str:
+def build(force: bool = False, extra: list[str] | None = None, jobs: int | None = None,
+          variant: str | None = None) -> str:
     """Compile every csrc/ unit for sm_103a and link libhrm.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
-    extra = list(extra or [])
+    lib = lib_path(variant)
+    if not force and up_to_date(variant):
+        return lib
+    out = os.path.dirname(lib)
+    os.makedirs(out, exist_ok=True)
+    extra = list(extra or []) + VARIANTS.get(variant or "", [])
     srcs = sources()
     jobs = jobs or min(len(srcs), max(1, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + ".tmp.%d" % os.getpid()
+        objs = list(ex.map(lambda s: _compile(s, extra, out), srcs))
+    tmp = lib + ".tmp.%d" % os.getpid()
     cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr[-4000:]))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv,
-                extra=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else None))
+                extra=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else None,
+                variant="count" if "--count" in sys.argv else None))

@@ -117,16 +117,29 @@ int slots_for(int tw, int r, int cw, size_t budget) {
 }
 
 size_t plan_smem(const PlanH& p, int r) {
-    return hist_smem_bytes(32 * p.ppl, r, p.nslots, p.cw, p.ring, p.es);
+    return hist_smem_bytes(BLOCK_THREADS * p.ppl, r, p.nslots, p.cw, p.ring, p.es);
 }
 
-// Fill slots (and the ring decision) for a given per-warp shared-memory budget.
+// Fill slots (and the ring decision) for a given per-tile shared-memory budget.
 static void size_slots(PlanH& p, int dims, int r, size_t budget) {
-    const int tw = 32 * p.ppl;
+    const int tw = BLOCK_THREADS * p.ppl;
     const size_t ring = hist_ring_bytes(tw, r, p.es);
-    p.ring = (dims == 2 && ring * 3 <= budget) ? 1 : 0;
-    const size_t rest = budget - (p.ring ? ring : 0);
+    p.ring = (dims == 2 && p.cw == 1 && ring * 3 <= budget) ? 1 : 0;
+    const size_t rest = budget > (p.ring ? ring : 0) ? budget - (p.ring ? ring : 0) : 0;
     p.nslots = std::max(2, std::min(slots_for(tw, r, p.cw, rest), MAX_SLOTS));
+}
+
+static int strip_length(int W, int lines, int walk, int r, int tw, size_t smem, const DeviceInfo& di) {
+    int bps = (int)(di.smem_per_sm / (smem + 1024));
+    bps = std::max(1, std::min(bps, di.max_blocks_per_sm));
+    const long tiles_x = (W + tw - 1) / tw;
+    const long target = (long)di.num_sms * bps * 2;
+    long sh = (walk * tiles_x * (long)lines + target - 1) / target;
+    const long n = 2L * r + 1;
+    sh = std::max(sh, std::min(2 * n, 64L));
+    sh = std::max(sh, 8L);
+    sh = std::min(sh, (long)walk);
+    return (int)std::max(1L, sh);
 }
 
 PlanH default_plan(int dims, int es, int W, int lines, int walk, int r, const DeviceInfo& di) {
@@ -134,36 +147,21 @@ PlanH default_plan(int dims, int es, int W, int lines, int walk, int r, const De
     p.es = es;
     p.path = (dims == 2 && r <= 2) ? 1 : 2;
     p.cw = counter_width(dims, r);
-    // narrow tiles at small radii keep the per-row node working set in the slot cache
-    p.ppl = (W <= 64 || r <= 16) ? 2 : 4;
-    const int tw = 32 * p.ppl;
-    // shared memory budget per warp: aim for ~6 resident warps per SM
-    size_t budget = (size_t)di.smem_per_sm / 6 - 1024;
+    p.ppl = 1;  // 128 outputs per tile
+    // shared memory per tile: about three resident tiles (12 warps) per SM
+    const size_t budget = std::min((size_t)di.smem_optin, (size_t)di.smem_per_sm / 3 - 1024);
     size_slots(p, dims, r, budget);
-    while (p.nslots < 4 && budget + 4096 <= (size_t)di.smem_optin) {
-        budget += 4096;
-        size_slots(p, dims, r, budget);
-    }
-    const size_t smem = plan_smem(p, r);
-    int wps = (int)(di.smem_per_sm / (smem + 1024));
-    wps = std::max(1, std::min(wps, di.max_blocks_per_sm));
-    const long tiles_x = (W + tw - 1) / tw;
-    const long target = (long)di.num_sms * wps * 2;
-    long sh = (walk * tiles_x * (long)lines + target - 1) / target;
-    const long n = 2L * r + 1;
-    sh = std::max(sh, std::min(2 * n, 64L));
-    sh = std::max(sh, 8L);
-    sh = std::min(sh, (long)walk);
-    p.sh = (int)std::max(1L, sh);
+    p.sh = strip_length(W, lines, walk, r, BLOCK_THREADS * p.ppl, plan_smem(p, r), di);
     return p;
 }
 
-static void apply_plan(PlanH& p, const hrm_plan& hp, int dims, int r, int walk) {
-    if (hp.tile_width == 64 || hp.tile_width == 128 || hp.tile_width == 256) p.ppl = hp.tile_width / 32;
-    if (p.cw == 2 && p.ppl > 4) p.ppl = 4;
-    if (hp.strip_height > 0) p.sh = std::min(hp.strip_height, walk);
+static void apply_plan(PlanH& p, const hrm_plan& hp, int dims, int W, int lines, int walk, int r,
+                       const DeviceInfo& di) {
+    if (hp.tile_width == BLOCK_THREADS || hp.tile_width == 2 * BLOCK_THREADS) p.ppl = hp.tile_width / BLOCK_THREADS;
     if (hp.slot_kbytes > 0) size_slots(p, dims, r, (size_t)hp.slot_kbytes * 1024);
     else size_slots(p, dims, r, plan_smem(p, r));
+    p.sh = hp.strip_height > 0 ? std::min(hp.strip_height, walk)
+                               : strip_length(W, lines, walk, r, BLOCK_THREADS * p.ppl, plan_smem(p, r), di);
     if (hp.path == 1 || hp.path == 2) p.path = hp.path;
 }
 
@@ -174,12 +172,12 @@ PlanH resolve_plan(int dtype, int dims, int W, int H, int D, int r, unsigned fla
     const int es = dtype == HRM_U16 ? 2 : 1;
     PlanH p = default_plan(dims, es, W, lines, walk, r, di);
     hrm_plan hp;
-    if (plan_lookup(ProblemKey{dtype, dims, W, H, D, r, flags}, &hp)) apply_plan(p, hp, dims, r, walk);
-    if (force) apply_plan(p, *force, dims, r, walk);
+    if (plan_lookup(ProblemKey{dtype, dims, W, H, D, r, flags}, &hp)) apply_plan(p, hp, dims, W, lines, walk, r, di);
+    if (force) apply_plan(p, *force, dims, W, lines, walk, r, di);
     // the shared-memory plan must fit the device
     while (p.nslots > 2 && plan_smem(p, r) > (size_t)di.smem_optin) --p.nslots;
     if (plan_smem(p, r) > (size_t)di.smem_optin) p.ring = 0;
-    while (p.ppl > 2 && plan_smem(p, r) > (size_t)di.smem_optin) p.ppl /= 2;
+    while (p.ppl > 1 && plan_smem(p, r) > (size_t)di.smem_optin) p.ppl /= 2;
     return p;
 }
 
@@ -241,7 +239,7 @@ int make_hist_job(const Image& im, int r, uint32_t K, unsigned flags, int drop_b
     j.sh = p.sh;
     j.nslots = p.nslots;
     j.ring = p.ring;
-    const int tw = 32 * p.ppl;
+    const int tw = BLOCK_THREADS * p.ppl;
     const int walk = im.dims == 3 ? im.D : im.H;
     const int lines = im.dims == 3 ? im.H : 1;
     j.tiles_x = (im.W + tw - 1) / tw;
@@ -387,7 +385,7 @@ int hrm_get_plan(int dtype, int dims, int width, int height, int depth, int radi
     if (plan_lookup(k, plan)) return HRM_OK;
     const DeviceInfo& di = device_info();
     PlanH p = resolve_plan(dtype, dims, width, height, depth, radius, flags, di, nullptr);
-    plan->tile_width = 32 * p.ppl;
+    plan->tile_width = BLOCK_THREADS * p.ppl;
     plan->strip_height = p.sh;
     plan->slot_kbytes = (int)((plan_smem(p, radius) + 1023) / 1024);
     plan->path = p.path;
@@ -398,8 +396,8 @@ int hrm_set_plan(int dtype, int dims, int width, int height, int depth, int radi
                  const hrm_plan* plan) {
     if (!plan) return fail(HRM_EINVAL, "null plan");
     if (dims != 2 && dims != 3) return fail(HRM_EINVAL, "dims must be 2 or 3");
-    if (plan->tile_width != 0 && plan->tile_width != 64 && plan->tile_width != 128 && plan->tile_width != 256)
-        return fail(HRM_EINVAL, "tile_width must be 64, 128 or 256");
+    if (plan->tile_width != 0 && plan->tile_width != 128 && plan->tile_width != 256)
+        return fail(HRM_EINVAL, "tile_width must be 128 or 256");
     if (plan->path < 0 || plan->path > 2) return fail(HRM_EINVAL, "path must be 0, 1 or 2");
     plan_store(ProblemKey{dtype, dims, width, height, depth, radius, flags}, *plan);
     return HRM_OK;

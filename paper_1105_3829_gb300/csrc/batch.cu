@@ -82,7 +82,9 @@ __global__ void batch_minmax(const LevelItem* items, int n) {
 __device__ void run_item(const BatchItem& it, int tile, unsigned char* sm) {
     const HistJob& j = it.job;
     if (it.kind != ITEM_HIST) {
-        const int tx = tile % it.tiles_x_s, ty = tile / it.tiles_x_s;
+        // a block item holds BLOCK_WARPS selection-network warp tiles
+        const int wt = tile * BLOCK_WARPS + (int)(threadIdx.x >> 5);
+        const int tx = wt % it.tiles_x_s, ty = wt / it.tiles_x_s;
         if (it.kind == ITEM_SORT3) {
             if (j.elem == 1) sortnet3x3_tile<uint8_t>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);
             else sortnet3x3_tile<uint16_t>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);
@@ -95,25 +97,24 @@ __device__ void run_item(const BatchItem& it, int tile, unsigned char* sm) {
 #define HRM_CASE(T, P, C) \
     if (j.ppl == P && j.cw == C) { hist_tile<T, P, C>(j, tile, sm); return; }
     if (j.elem == 1) {
-        HRM_CASE(uint8_t, 2, 1) HRM_CASE(uint8_t, 4, 1) HRM_CASE(uint8_t, 8, 1)
-        HRM_CASE(uint8_t, 2, 2) HRM_CASE(uint8_t, 4, 2)
+        HRM_CASE(uint8_t, 1, 1) HRM_CASE(uint8_t, 2, 1) HRM_CASE(uint8_t, 1, 2) HRM_CASE(uint8_t, 2, 2)
     } else {
-        HRM_CASE(uint16_t, 2, 1) HRM_CASE(uint16_t, 4, 1) HRM_CASE(uint16_t, 8, 1)
-        HRM_CASE(uint16_t, 2, 2) HRM_CASE(uint16_t, 4, 2)
+        HRM_CASE(uint16_t, 1, 1) HRM_CASE(uint16_t, 2, 1) HRM_CASE(uint16_t, 1, 2) HRM_CASE(uint16_t, 2, 2)
     }
 #undef HRM_CASE
-    if ((threadIdx.x & 31) == 0) set_error(j.err, DEV_BAD_JOB);
+    if (threadIdx.x == 0) set_error(j.err, DEV_BAD_JOB);
 }
 
-__global__ void __launch_bounds__(32) batch_kernel(const BatchItem* __restrict__ items,
-                                                   const unsigned* __restrict__ tile_off, int nitems,
-                                                   unsigned* counter, unsigned total) {
+__global__ void __launch_bounds__(BLOCK_THREADS, 3) batch_kernel(const BatchItem* __restrict__ items,
+                                                              const unsigned* __restrict__ tile_off, int nitems,
+                                                              unsigned* counter, unsigned total) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
+    __shared__ unsigned s_next;
     for (;;) {
-        unsigned t = 0;
-        if (lane == 0) t = atomicAdd(counter, 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
+        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1u);
+        __syncthreads();
+        const unsigned t = s_next;
+        __syncthreads();  // every thread has read s_next before the next fetch
         if (t >= total) break;
         int lo = 0, hi = nitems - 1;  // last item whose first tile is <= t
         while (lo < hi) {
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(32) batch_kernel(const BatchItem* __restrict__
         }
         const BatchItem it = items[lo];
         run_item(it, (int)(t - tile_off[lo]), smem);
-        __syncwarp();
+        __syncthreads();  // the tile's shared memory is free again
     }
 }
 
@@ -139,6 +140,13 @@ struct BatchDev {
     unsigned* err = nullptr;
     int cap = 0;
     void* base = nullptr;
+    // pinned staging ring for asynchronous table uploads (a pageable source
+    // could make cudaMemcpyAsync wait for the stream)
+    static constexpr int NSTAGE = 4;
+    unsigned char* stage[NSTAGE] = {};
+    cudaEvent_t stage_ev[NSTAGE] = {};
+    size_t stage_cap = 0;
+    int stage_next = 0;
 };
 
 static int batchdev_alloc(BatchDev& b, int cap) {
@@ -165,6 +173,10 @@ static int batchdev_alloc(BatchDev& b, int cap) {
 
 static void batchdev_free(BatchDev& b) {
     if (b.base) cudaFree(b.base);
+    for (int i = 0; i < BatchDev::NSTAGE; ++i) {
+        if (b.stage_ev[i]) cudaEventSynchronize(b.stage_ev[i]), cudaEventDestroy(b.stage_ev[i]);
+        if (b.stage[i]) cudaFreeHost(b.stage[i]);
+    }
     b = BatchDev{};
 }
 
@@ -214,7 +226,8 @@ static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, Batch
             h.W = im.W;
             h.H = im.H;
             h.elem = es;
-            h.ntiles = t.it.tiles_x_s * ((im.H + 31) / 32);
+            const int wtiles = t.it.tiles_x_s * ((im.H + 31) / 32);
+            h.ntiles = (wtiles + BLOCK_WARPS - 1) / BLOCK_WARPS;
             t.cost = 1.0;
         } else {
             const LevelDesc* desc = nullptr;
@@ -232,7 +245,7 @@ static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, Batch
             if (rc) return rc;
             bp.smem = std::max(bp.smem, plan_smem(p, jb.radius));
             // expensive tiles first: work per tile grows with the strip and the window
-            t.cost = (double)p.sh * (32.0 * p.ppl + 2.0 * jb.radius) * (jb.dims == 3 ? n : 1);
+            t.cost = (double)p.sh * ((double)BLOCK_THREADS * p.ppl + 2.0 * jb.radius) * (jb.dims == 3 ? n : 1);
         }
         tmp.push_back(t);
     }
@@ -288,20 +301,51 @@ static int enqueue_batch(const BatchPlan& bp, const BatchDev& dev, cudaStream_t 
     }
     int per_sm = std::max(1, std::min(di.max_blocks_per_sm, (int)(di.smem_per_sm / (smem + 1024))));
     unsigned grid = (unsigned)std::min<long>((long)di.num_sms * per_sm, (long)bp.total);
-    batch_kernel<<<grid, 32, smem, st>>>(dev.items, dev.offs, (int)bp.items.size(), dev.counter, bp.total);
+    batch_kernel<<<grid, BLOCK_THREADS, smem, st>>>(dev.items, dev.offs, (int)bp.items.size(), dev.counter, bp.total);
     e = cudaGetLastError();
     return e == cudaSuccess ? HRM_OK : cuda_fail(e, "batch kernel launch");
 }
 
-static int upload_plan(const BatchPlan& bp, const BatchDev& dev, cudaStream_t st, bool sync) {
+static int upload_plan(const BatchPlan& bp, BatchDev& dev, cudaStream_t st, bool sync) {
     cudaError_t e = cudaSuccess;
-    auto cp = [&](void* d, const void* h, size_t n) {
-        if (!n || e != cudaSuccess) return;
-        e = sync ? cudaMemcpy(d, h, n, cudaMemcpyHostToDevice) : cudaMemcpyAsync(d, h, n, cudaMemcpyHostToDevice, st);
-    };
-    cp(dev.items, bp.items.data(), sizeof(BatchItem) * bp.items.size());
-    cp(dev.offs, bp.offs.data(), sizeof(unsigned) * bp.offs.size());
-    cp(dev.litems, bp.levels.data(), sizeof(LevelItem) * bp.levels.size());
+    const size_t n_items = sizeof(BatchItem) * bp.items.size(), n_offs = sizeof(unsigned) * bp.offs.size(),
+                 n_lev = sizeof(LevelItem) * bp.levels.size();
+    if (sync) {
+        auto cp = [&](void* d, const void* h, size_t n) {
+            if (n && e == cudaSuccess) e = cudaMemcpy(d, h, n, cudaMemcpyHostToDevice);
+        };
+        cp(dev.items, bp.items.data(), n_items);
+        cp(dev.offs, bp.offs.data(), n_offs);
+        cp(dev.litems, bp.levels.data(), n_lev);
+        return e == cudaSuccess ? HRM_OK : cuda_fail(e, "batch table upload");
+    }
+    const size_t need = n_items + n_offs + n_lev;
+    if (dev.stage_cap < need) {
+        for (int i = 0; i < BatchDev::NSTAGE; ++i) {
+            if (dev.stage_ev[i]) cudaEventSynchronize(dev.stage_ev[i]);
+            if (dev.stage[i]) cudaFreeHost(dev.stage[i]);
+            dev.stage[i] = nullptr;
+            e = cudaMallocHost((void**)&dev.stage[i], need);
+            if (e != cudaSuccess) return fail(HRM_ENOMEM, "pinned staging buffer");
+            if (!dev.stage_ev[i]) {
+                e = cudaEventCreateWithFlags(&dev.stage_ev[i], cudaEventDisableTiming);
+                if (e != cudaSuccess) return cuda_fail(e, "staging event");
+            }
+        }
+        dev.stage_cap = need;
+    }
+    const int k = dev.stage_next;
+    dev.stage_next = (k + 1) % BatchDev::NSTAGE;
+    e = cudaEventSynchronize(dev.stage_ev[k]);  // that slot's previous upload has been consumed
+    if (e != cudaSuccess) return cuda_fail(e, "staging event wait");
+    unsigned char* h = dev.stage[k];
+    memcpy(h, bp.items.data(), n_items);
+    memcpy(h + n_items, bp.offs.data(), n_offs);
+    if (n_lev) memcpy(h + n_items + n_offs, bp.levels.data(), n_lev);
+    if (n_items) e = cudaMemcpyAsync(dev.items, h, n_items, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_offs) e = cudaMemcpyAsync(dev.offs, h + n_items, n_offs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && n_lev) e = cudaMemcpyAsync(dev.litems, h + n_items + n_offs, n_lev, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(dev.stage_ev[k], st);
     return e == cudaSuccess ? HRM_OK : cuda_fail(e, "batch table upload");
 }
 

@@ -7,7 +7,7 @@
 namespace hrm {
 
 template <typename T, int PPL, int CW>
-__global__ void __launch_bounds__(32) hist_kernel(HistJob job) {
+__global__ void __launch_bounds__(BLOCK_THREADS, 3) hist_kernel(HistJob job) {
     extern __shared__ __align__(16) unsigned char smem[];
     hist_tile<T, PPL, CW>(job, (int)blockIdx.x, smem);
 }
@@ -19,7 +19,7 @@ static cudaError_t launch_one(const HistJob& job, size_t smem, cudaStream_t st) 
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    fn<<<job.ntiles, 32, smem, st>>>(job);
+    fn<<<job.ntiles, BLOCK_THREADS, smem, st>>>(job);
     return cudaGetLastError();
 }
 
@@ -27,22 +27,36 @@ template <typename T>
 static cudaError_t launch_t(const HistJob& job, size_t smem, cudaStream_t st) {
     if (job.cw == 1) {
         switch (job.ppl) {
+            case 1: return launch_one<T, 1, 1>(job, smem, st);
             case 2: return launch_one<T, 2, 1>(job, smem, st);
-            case 4: return launch_one<T, 4, 1>(job, smem, st);
-            case 8: return launch_one<T, 8, 1>(job, smem, st);
         }
     } else if (job.cw == 2) {
         switch (job.ppl) {
+            case 1: return launch_one<T, 1, 2>(job, smem, st);
             case 2: return launch_one<T, 2, 2>(job, smem, st);
-            case 4: return launch_one<T, 4, 2>(job, smem, st);
         }
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_hist(const HistJob& job, cudaStream_t st) {
-    const size_t smem = hist_smem_bytes(32 * job.ppl, job.r, job.nslots, job.cw, job.ring, job.elem);
+    const size_t smem = hist_smem_bytes(BLOCK_THREADS * job.ppl, job.r, job.nslots, job.cw, job.ring, job.elem);
     return job.elem == 1 ? launch_t<uint8_t>(job, smem, st) : launch_t<uint16_t>(job, smem, st);
 }
 
 }  // namespace hrm
+
+#ifdef HRM_COUNT_OPS
+// Instrumented builds only: read (and optionally clear) the device counters of
+// the single-image histogram kernel.
+extern "C" int hrm_debug_counters(unsigned long long* out, int n, int reset) {
+    if (n > hrm::CNT_NUM) n = hrm::CNT_NUM;
+    cudaDeviceSynchronize();
+    if (cudaMemcpyFromSymbol(out, hrm::g_hrm_counters, sizeof(unsigned long long) * n) != cudaSuccess) return -3;
+    if (reset) {
+        unsigned long long z[hrm::CNT_NUM] = {};
+        cudaMemcpyToSymbol(hrm::g_hrm_counters, z, sizeof(z));
+    }
+    return 0;
+}
+#endif

@@ -26,22 +26,76 @@ struct LevelDesc {
 };
 static_assert(sizeof(LevelDesc) == 128, "LevelDesc layout");
 
+// Optional instrumentation (build with -DHRM_COUNT_OPS): per-phase cycle and
+// event counters, accumulated per warp and flushed once per tile.  The normal
+// library compiles all of it away.
+enum CountId {
+    CNT_TILES = 0, CNT_ROWS, CNT_CYC_TOTAL, CNT_CYC_INIT, CNT_CYC_COLUMNS, CNT_CYC_RESOLVE,
+    CNT_CYC_INSTALL, CNT_CYC_WINDOW, CNT_CYC_ADVANCE, CNT_INSTALLS, CNT_ROUNDS, CNT_PREFIXES,
+    CNT_DIRECT_ROUNDS, CNT_LEVELS, CNT_NUM
+};
+#ifdef HRM_COUNT_OPS
+static __device__ unsigned long long g_hrm_counters[CNT_NUM];
+struct OpCounters {
+    unsigned long long v[CNT_NUM];
+    long long t0;
+    __device__ void reset() { for (int i = 0; i < CNT_NUM; ++i) v[i] = 0; }
+    __device__ void add(int i, unsigned long long x) { v[i] += x; }
+    __device__ void mark() { t0 = clock64(); }
+    __device__ void lap(int i) { long long t = clock64(); v[i] += (unsigned long long)(t - t0); t0 = t; }
+    __device__ void flush() {
+        if ((threadIdx.x & 31) == 0)
+            for (int i = 0; i < CNT_NUM; ++i) if (v[i]) atomicAdd(&g_hrm_counters[i], v[i]);
+    }
+};
+#else
+struct OpCounters {
+    __device__ void reset() {}
+    __device__ void add(int, unsigned long long) {}
+    __device__ void mark() {}
+    __device__ void lap(int) {}
+    __device__ void flush() {}
+};
+#endif
+
 constexpr uint32_t KEY_NONE = 0xFFFFFFFFu;
 constexpr int HASH_SIZE = 64;
 constexpr int MAX_SLOTS = 32;
-constexpr int META_BYTES = 1024;  // per-warp metadata block (see Meta)
+constexpr int META_BYTES = 5120;  // per-tile metadata block (see Meta)
+constexpr int REQ_MAX = 256;      // node requests per round
+constexpr int PREQ_SIZE = 128;    // pending-request hash (deduplicates requests)
+constexpr uint8_t NO_SLOT = 0xFF;
 
-// Per-warp metadata in shared memory.
+// Per-warp metadata in shared memory.  Resident nodes are found through
+// direct tables for the first two levels below the root (level 1: coarse
+// interval c; level 2: c and the first 4-bit digit) and through a small hash
+// for deeper levels (16-bit data only).
 struct Meta {
     uint32_t e[17];        // coarse edges
     uint32_t D[16];        // sub-tree bits per coarse interval
     uint32_t key[MAX_SLOTS];
     uint32_t stamp[MAX_SLOTS];
     uint32_t pin[MAX_SLOTS];
-    uint32_t hash[HASH_SIZE];
+    uint32_t hash[HASH_SIZE];  // levels >= 3: (key << 8) | slot
     uint32_t lmask[8];     // lmask[l] bit c: a slot at level l for coarse c exists; lmask[0] = OR of all
     int32_t ushift;        // >= 0: uniform shift; -1: adaptive
-    uint32_t pad[3];
+    uint32_t ndeep;        // resident slots at levels >= 3
+    uint32_t pad[2];
+    uint8_t lut1[16];      // level 1: c -> slot
+    uint8_t lut2[256];     // level 2: (c << 4) | d1 -> slot
+    // block coordination (one tile per thread block)
+    uint32_t preq[PREQ_SIZE];   // pending requests of this round (keys)
+    uint32_t req[REQ_MAX];      // distinct requested keys in arrival order
+    uint32_t nreq;
+    uint32_t nbuild;
+    uint32_t deferred;          // some requests did not get a slot this round
+    uint32_t used;              // slots used by the outputs resolved this round
+    uint32_t build_slot[MAX_SLOTS];
+    uint32_t build_key[MAX_SLOTS];
+    int32_t span_lo[MAX_SLOTS];
+    int32_t span_hi[MAX_SLOTS];
+    uint32_t wtot[8][8];        // per-warp totals of the block prefix scan
+    uint32_t maxres;            // most outputs of one thread resolved this round
 };
 static_assert(sizeof(Meta) <= META_BYTES, "Meta too large");
 
@@ -60,11 +114,11 @@ __device__ __forceinline__ int coarse_of(const Meta& m, uint32_t v) {
     return c;
 }
 
-__device__ __forceinline__ int slot_lookup(const Meta& m, uint32_t key) {
+__device__ __forceinline__ int hash_lookup(const Meta& m, uint32_t key) {
     uint32_t h = hash_of(key);
 #pragma unroll 1
     for (int i = 0; i < HASH_SIZE; ++i) {
-        uint32_t ent = m.hash[h];
+        const uint32_t ent = m.hash[h];
         if (ent == KEY_NONE) return -1;
         if ((ent >> 8) == key) return (int)(ent & 0xFFu);
         h = (h + 1) & (HASH_SIZE - 1);
@@ -72,25 +126,106 @@ __device__ __forceinline__ int slot_lookup(const Meta& m, uint32_t key) {
     return -1;
 }
 
-// Rebuild the hash table and level masks from m.key[] (whole warp).
-__device__ __forceinline__ void rehash(Meta& m, int nslots) {
+// Slot holding node (level >= 1, coarse interval c, digit prefix pre), or -1.
+__device__ __forceinline__ int slot_lookup(const Meta& m, int level, int c, uint32_t pre) {
+    int s;
+    if (level == 1) s = m.lut1[c];
+    else if (level == 2) s = m.lut2[(c << 4) | (int)(pre & 15u)];
+    else return m.ndeep ? hash_lookup(m, node_key(level, c, pre)) : -1;
+    return s == NO_SLOT ? -1 : s;
+}
+
+__device__ __forceinline__ int slot_lookup(const Meta& m, uint32_t key) {
+    return slot_lookup(m, (int)(key >> 20), (int)((key >> 16) & 15), key & 0xFFFFu);
+}
+
+// Reset all tables with only the root (slot 0) resident (call from warp 0).
+__device__ __forceinline__ void slots_reset(Meta& m) {
     const int lane = threadIdx.x & 31;
+    m.key[lane] = lane == 0 ? 0u : KEY_NONE;
+    m.stamp[lane] = lane == 0 ? 0xFFFFFFFFu : 0u;
+    m.pin[lane] = 0;
     m.hash[lane] = KEY_NONE;
     m.hash[lane + 32] = KEY_NONE;
+    if (lane < 8) m.lmask[lane] = 0;
+    if (lane < 16) m.lut1[lane] = NO_SLOT;
+    reinterpret_cast<uint32_t*>(m.lut2)[lane] = 0xFFFFFFFFu;
+    reinterpret_cast<uint32_t*>(m.lut2)[lane + 32] = 0xFFFFFFFFu;
+#pragma unroll
+    for (int i = lane; i < PREQ_SIZE; i += 32) m.preq[i] = KEY_NONE;
+    m.span_lo[lane] = 0x7FFFFFFF;
+    m.span_hi[lane] = -1;
+    if (lane == 0) {
+        m.ndeep = 0;
+        m.nreq = 0;
+        m.nbuild = 0;
+        m.deferred = 0;
+        m.used = 0;
+        m.maxres = 0;
+    }
+    __syncwarp();
+}
+
+// Record a missing node for this round; duplicates collapse through a small
+// hash of pending keys.  A request that finds the table full is simply not
+// recorded (its outputs retry next round; the first request always fits).
+__device__ __forceinline__ void request_node(Meta& m, uint32_t key) {
+    uint32_t h = hash_of(key) & (PREQ_SIZE - 1);
+    for (int i = 0; i < PREQ_SIZE; ++i) {
+        const uint32_t prev = atomicCAS(&m.preq[h], KEY_NONE, key);
+        if (prev == KEY_NONE) {
+            const uint32_t at = atomicAdd(&m.nreq, 1u);
+            if (at < REQ_MAX) m.req[at] = key;
+            return;
+        }
+        if (prev == key) return;
+        h = (h + 1) & (PREQ_SIZE - 1);
+    }
+}
+
+// Give slot v to node nk (whole warp): update the direct tables in O(1), the
+// hash only when a level >= 3 node enters or leaves, and the level masks.
+__device__ __forceinline__ void slot_assign(Meta& m, int nslots, int v, uint32_t nk) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t ok = m.key[v];
+    const int ol = ok == KEY_NONE ? 0 : (int)(ok >> 20), nl = (int)(nk >> 20);
     __syncwarp();
     if (lane == 0) {
-        uint32_t lm[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int s = 1; s < nslots; ++s) {
-            uint32_t k = m.key[s];
-            if (k == KEY_NONE) continue;
-            int l = (int)(k >> 20), c = (int)((k >> 16) & 15);
-            lm[l] |= 1u << c;
-            lm[0] |= 1u << c;
-            uint32_t h = hash_of(k);
-            while (m.hash[h] != KEY_NONE) h = (h + 1) & (HASH_SIZE - 1);
-            m.hash[h] = (k << 8) | (uint32_t)s;
-        }
-        for (int l = 0; l < 8; ++l) m.lmask[l] = lm[l];
+        if (ol == 1) m.lut1[(ok >> 16) & 15] = NO_SLOT;
+        if (ol == 2) m.lut2[(((ok >> 16) & 15) << 4) | (ok & 15)] = NO_SLOT;
+        if (nl == 1) m.lut1[(nk >> 16) & 15] = (uint8_t)v;
+        if (nl == 2) m.lut2[(((nk >> 16) & 15) << 4) | (nk & 15)] = (uint8_t)v;
+        m.key[v] = nk;
+    }
+    __syncwarp();
+    // level masks from all slot keys
+    const uint32_t k = (lane > 0 && lane < nslots) ? m.key[lane] : KEY_NONE;
+    const int kl = k == KEY_NONE ? 0 : (int)(k >> 20);
+    const uint32_t bit = k == KEY_NONE ? 0u : 1u << ((k >> 16) & 15);
+    uint32_t any = 0;
+#pragma unroll
+    for (int l = 1; l < 5; ++l) {
+        const uint32_t ml = __reduce_or_sync(0xffffffffu, kl == l ? bit : 0u);
+        if (lane == 0) m.lmask[l] = ml;
+        any |= ml;
+    }
+    const unsigned deep = __popc(__ballot_sync(0xffffffffu, kl >= 3));
+    if (lane == 0) {
+        m.lmask[0] = any;
+        m.ndeep = deep;
+    }
+    if (ol >= 3 || nl >= 3) {  // rebuild the hash of deep nodes
+        m.hash[lane] = KEY_NONE;
+        m.hash[lane + 32] = KEY_NONE;
+        __syncwarp();
+        if (lane == 0)
+            for (int s = 1; s < nslots; ++s) {
+                const uint32_t kk = m.key[s];
+                if (kk == KEY_NONE || (kk >> 20) < 3) continue;
+                uint32_t h = hash_of(kk);
+                while (m.hash[h] != KEY_NONE) h = (h + 1) & (HASH_SIZE - 1);
+                m.hash[h] = (kk << 8) | (uint32_t)s;
+            }
     }
     __syncwarp();
 }

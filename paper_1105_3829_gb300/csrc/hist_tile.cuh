@@ -1,10 +1,13 @@
-// hist_tile.cuh -- hierarchical recursive running median: one warp, one tile.
+// hist_tile.cuh -- hierarchical recursive running median: one thread block,
+// one tile.
 //
-// A tile is a row of TW = 32*PPL outputs along x that the warp walks along
-// the "walk axis" (y for 2D images, z for 3D volumes): Section III, column
-// IOTs slid along the walk axis, the window IOT assembled across x.
+// A tile is a row of TW = 32*W*PPL outputs along x that a block of W warps
+// walks along the "walk axis" (y for 2D images, z for 3D volumes): Section
+// III, column IOTs slid along the walk axis, the window IOT assembled across
+// x.  Every thread owns PPL outputs of each row and about 1/(32W) of the
+// columns; the phases of a row are separated by block barriers.
 //
-// Per warp, in shared memory:
+// Per block, in shared memory:
 //   * "column" histograms for the TW + 2r columns the tile's windows touch.
 //     In 2D a column is the n pixels of image column x inside the window's
 //     rows; in 3D it is the n x n slab of voxels (rows y-r..y+r, slices
@@ -40,6 +43,9 @@
 
 namespace hrm {
 
+constexpr int BLOCK_WARPS = 4;     // warps per tile
+constexpr int BLOCK_THREADS = 32 * BLOCK_WARPS;
+
 struct HistJob {
     const unsigned char* src;
     unsigned char* dst;
@@ -57,7 +63,7 @@ struct HistJob {
     int fixed_shift;
     int drop_bits;           // reduced precision: stop once <= drop_bits bits remain (0 = exact)
     int elem;                // 1 or 2 bytes per value
-    int ppl;                 // pixels per lane
+    int ppl;                 // outputs per thread (TW = 32 * BLOCK_WARPS * ppl)
     int cw;                  // counter width in bytes (1 or 2)
     int ring;                // 2D only: stage the last n+1 input rows in shared memory
     unsigned* err;           // device error word (may be null)
@@ -143,86 +149,106 @@ __device__ __forceinline__ uint32_t geo_ld(const Geo& g, int t, int i, int gx) {
 
 __device__ __forceinline__ int ring_idx(int u, int M) { return (u + M) % M; }
 
-// Build slot s for node `key` at walk position t from the staged values of
-// every column: from the shared-memory ring of the last n+1 rows when present
-// (2D), else from global memory with the lane's columns interleaved so that
-// several independent loads are in flight.
-template <typename T, int CW>
-__device__ void build_slot(const HistJob& a, const Geo& g, const Meta& m, unsigned char* slots, int NC,
-                           int x0, int t, int s, uint32_t key, const T* ring) {
-    const int lane = threadIdx.x & 31;
-    const int r = a.r;
-    const int level = (int)(key >> 20);
-    const int c = (int)((key >> 16) & 15);
-    const uint32_t pre = key & 0xFFFFu;
-    uint32_t lo = 0, hi = 0xFFFFFFFFu;
-    int dshift = 0;
-    if (level > 0) {
-        const int top = (int)m.D[c] - 4 * (level - 1);
+// Node geometry: value range [lo, hi) of node `key` and the shift that turns
+// (v - lo) into its child index (level 0: the coarse interval).
+struct NodeRange {
+    int level;
+    uint32_t lo, hi;
+    int dshift;
+};
+
+__device__ __forceinline__ NodeRange node_range(const Meta& m, uint32_t key) {
+    NodeRange nr;
+    nr.level = (int)(key >> 20);
+    nr.lo = 0;
+    nr.hi = 0xFFFFFFFFu;
+    nr.dshift = 0;
+    if (nr.level > 0) {
+        const int c = (int)((key >> 16) & 15);
+        const uint32_t pre = key & 0xFFFFu;
+        const int top = (int)m.D[c] - 4 * (nr.level - 1);
         const int b = min(4, top);
-        lo = m.e[c] + (pre << top);
-        hi = min(lo + (1u << top), m.e[c + 1]);
-        dshift = top - b;
+        nr.lo = m.e[c] + (pre << top);
+        nr.hi = min(nr.lo + (1u << top), m.e[c + 1]);
+        nr.dshift = top - b;
     }
-    auto digit = [&](uint32_t v) -> int {
-        if (level == 0) return coarse_of(m, v);
-        if (v < lo || v >= hi) return -1;
-        return (int)((v - lo) >> dshift);
-    };
-    if (ring) {
-        const int M = 2 * r + 2;
-        for (int cx = lane; cx < NC; cx += 32) {
-            uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    return nr;
+}
+
+__device__ __forceinline__ int node_digit(const Meta& m, const NodeRange& nr, uint32_t v) {
+    if (nr.level == 0) return coarse_of(m, v);
+    if (v < nr.lo || v >= nr.hi) return -1;
+    return (int)((v - nr.lo) >> nr.dshift);
+}
+
+// Build the records of m.nbuild new slots at walk position t (whole block):
+// work items (slot, column) are spread over the threads; values come from the
+// shared-memory ring when present (2D), else from global memory with eight
+// loads in flight per thread.
+template <typename T, int CW>
+__device__ void build_slots(const HistJob& a, const Geo& g, const Meta& m, unsigned char* slots, int NC,
+                            int x0, int t, const T* ring) {
+    const int r = a.r;
+    const int nb = (int)m.nbuild;
+    const int items = nb * NC;
+    const int nv = (2 * r + 1) * g.layer;  // values per column
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int b = it / NC, cx = it - b * NC;
+        const NodeRange nr = node_range(m, m.build_key[b]);
+        uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (ring) {
+            const int M = 2 * r + 2;
 #pragma unroll 4
             for (int tt = t - r; tt <= t + r; ++tt) {
-                const int d = digit((uint32_t)ring[(size_t)ring_idx(tt, M) * NC + cx]);
+                const int d = node_digit(m, nr, (uint32_t)ring[(size_t)ring_idx(tt, M) * NC + cx]);
                 if (d >= 0) reg_count<CW>(cnt, d);
             }
-            rec_store<CW>(slots + ((size_t)s * NC + cx) * 16 * CW, cnt);
-        }
-        return;
-    }
-    // global: process the lane's columns four at a time
-    for (int cb = lane; cb < NC; cb += 128) {
-        uint32_t cnt[4][8];
-        int gx[4];
+        } else {
+            const int gx = clampi(x0 - r + cx, 0, a.W - 1);
+            for (int q0 = 0; q0 < nv; q0 += 8) {
+                uint32_t v[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+                for (int u = 0; u < 8; ++u) {
+                    const int q = min(q0 + u, nv - 1);
+                    v[u] = geo_ld<T>(g, t - r + q / g.layer, q % g.layer, gx);
+                }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) cnt[j][k] = 0;
-            gx[j] = clampi(x0 - r + cb + 32 * j, 0, a.W - 1);
-        }
-        for (int tt = t - r; tt <= t + r; ++tt) {
-            for (int i = 0; i < g.layer; ++i) {
-                uint32_t v[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) v[j] = geo_ld<T>(g, tt, i, gx[j]);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int d = digit(v[j]);
-                    if (d >= 0) reg_count<CW>(cnt[j], d);
+                for (int u = 0; u < 8; ++u) {
+                    if (q0 + u >= nv) break;
+                    const int d = node_digit(m, nr, v[u]);
+                    if (d >= 0) reg_count<CW>(cnt, d);
                 }
             }
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (cb + 32 * j < NC) rec_store<CW>(slots + ((size_t)s * NC + cb + 32 * j) * 16 * CW, cnt[j]);
+        rec_store<CW>(slots + ((size_t)m.build_slot[b] * NC + cx) * 16 * CW, cnt);
     }
 }
 
-// Insert (+1) or remove (-1) value v of column cx in every resident node on its path.
+// Packed counter deltas of one record: word w of bin b gets +-(1 << lane_shift).
+// Adding the accumulated delta to the record in one step is exact whenever the
+// final counts are in range (the arithmetic is modulo 2^32 per word).
 template <int CW>
-__device__ __forceinline__ void column_update(const Meta& m, unsigned char* slots, int NC, int cx,
-                                              uint32_t v, int delta) {
-    const int c = coarse_of(m, v);
-    rec_bump<CW>(slots + (size_t)cx * 16 * CW, c, delta);
+__device__ __forceinline__ void delta_add(uint32_t (&dw)[4 * CW], int b, int sign) {
+    constexpr int NW = 4 * CW;  // words per record
+    constexpr int per = 4 / CW; // counters per word
+    const uint32_t inc = 1u << ((32 / per) * (b % per));
+    const int w = b / per;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) dw[k] += w == k ? (sign > 0 ? inc : 0u - inc) : 0u;
+}
+
+// Insert (+1) or remove (-1) value v of column cx in every resident node below
+// the root on its path (Section III-B: one counter per level).
+template <int CW>
+__device__ __forceinline__ void deep_update(const Meta& m, unsigned char* slots, int NC, int cx, uint32_t v,
+                                            int c, int delta) {
     if (!((m.lmask[0] >> c) & 1u)) return;
     const uint32_t u = v - m.e[c];
     const int D = (int)m.D[c];
     for (int level = 1; 4 * (level - 1) < D; ++level) {
         if (!((m.lmask[level] >> c) & 1u)) continue;
         const int top = D - 4 * (level - 1);
-        const int s = slot_lookup(m, node_key(level, c, u >> top));
+        const int s = slot_lookup(m, level, c, u >> top);
         if (s < 0) continue;
         const int b = min(4, top);
         const int d = (int)((u >> (top - b)) & ((1u << b) - 1u));
@@ -230,24 +256,41 @@ __device__ __forceinline__ void column_update(const Meta& m, unsigned char* slot
     }
 }
 
-// Inclusive prefix over columns [lo, hi] of slot s into pfx[1 .. m], pfx[0] = 0.
+// Block-wide inclusive prefix over columns [lo, hi] of slot s into
+// pfx[1 .. hi-lo+1] (pfx[0] = 0): each thread scans an odd-length chunk of
+// columns (odd so that a quarter-warp's 16-byte records fall in distinct
+// bank groups), then chunk totals are scanned across lanes and warps.
 template <int CW>
-__device__ __forceinline__ void slot_prefix(const unsigned char* slots, uint4* pfx, int NC, int s,
-                                            int lo, int hi) {
-    const int lane = threadIdx.x & 31;
+__device__ void block_prefix(Meta& m, const unsigned char* slots, uint4* pfx, int NC, int s, int lo, int hi) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nt = blockDim.x;
     const int mcols = hi - lo + 1;
-    // Odd chunk length: lanes read columns q records apart, and an odd q spreads
-    // the 16-byte records of a quarter-warp over distinct bank groups.
-    const int q = ((mcols + 31) >> 5) | 1;
-    const int c_begin = lo + lane * q;
+    const int q = ((mcols + nt - 1) / nt) | 1;
+    const int c_begin = lo + tid * q;
     const int c_end = min(c_begin + q, hi + 1);
     uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const unsigned char* base = slots + (size_t)s * NC * 16 * CW;
-    for (int cx = c_begin; cx < c_end; ++cx) {
-        rec_add<CW>(acc, base + (size_t)cx * 16 * CW);
-        uint4* p = pfx + 2 * (cx - lo + 1);
-        p[0] = make_uint4(acc[0], acc[1], acc[2], acc[3]);
-        p[1] = make_uint4(acc[4], acc[5], acc[6], acc[7]);
+    for (int c0 = c_begin; c0 < c_end; c0 += 4) {
+        uint4 rec[4][CW];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int cx = min(c0 + u, c_end - 1);
+#pragma unroll
+            for (int h = 0; h < CW; ++h) rec[u][h] = reinterpret_cast<const uint4*>(base + (size_t)cx * 16 * CW)[h];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (c0 + u >= c_end) break;
+            if (CW == 1) {
+                acc_add(acc, rec[u][0]);
+            } else {
+                acc[0] += rec[u][0].x; acc[1] += rec[u][0].y; acc[2] += rec[u][0].z; acc[3] += rec[u][0].w;
+                acc[4] += rec[u][CW - 1].x; acc[5] += rec[u][CW - 1].y; acc[6] += rec[u][CW - 1].z; acc[7] += rec[u][CW - 1].w;
+            }
+            uint4* p = pfx + 2 * (c0 + u - lo + 1);
+            p[0] = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+            p[1] = make_uint4(acc[4], acc[5], acc[6], acc[7]);
+        }
     }
     uint32_t inc[8];
 #pragma unroll
@@ -256,13 +299,21 @@ __device__ __forceinline__ void slot_prefix(const unsigned char* slots, uint4* p
     for (int off = 1; off < 32; off <<= 1) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, inc[k], off);
-            if (lane >= off) inc[k] += t;
+            const uint32_t tv = __shfl_up_sync(0xffffffffu, inc[k], off);
+            if (lane >= off) inc[k] += tv;
         }
     }
+    if (lane == 31) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) m.wtot[warp][k] = inc[k];
+    }
+    __syncthreads();
     uint32_t carry[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) carry[k] = inc[k] - acc[k];
+    for (int w = 0; w < warp; ++w)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) carry[k] += m.wtot[w][k];
     for (int cx = c_begin; cx < c_end; ++cx) {
         uint4* p = pfx + 2 * (cx - lo + 1);
         uint4 u0 = p[0], u1 = p[1];
@@ -271,17 +322,18 @@ __device__ __forceinline__ void slot_prefix(const unsigned char* slots, uint4* p
         p[0] = u0;
         p[1] = u1;
     }
-    if (lane == 0) {
+    if (tid == 0) {
         pfx[0] = make_uint4(0, 0, 0, 0);
         pfx[1] = make_uint4(0, 0, 0, 0);
     }
-    __syncwarp();
+    __syncthreads();
 }
 
 template <typename T, int PPL, int CW>
 __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
-    constexpr int TW = 32 * PPL;
-    const int lane = threadIdx.x & 31;
+    constexpr int NT = BLOCK_THREADS;
+    constexpr int TW = NT * PPL;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r = a.r;
     const int n = 2 * r + 1;
     const int NC = TW + 2 * r;
@@ -294,10 +346,16 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         strip = rest / a.H;
     }
     const int L = a.dims == 3 ? a.D : a.H;  // walk-axis length
+    {
+        // Strips at the two ends of the walk axis see clamped windows with
+        // noisier medians (more tree nodes per row): schedule them first.
+        const int nstrips = (L + a.sh - 1) / a.sh;
+        if (nstrips >= 3) strip = strip == 0 ? 0 : (strip == 1 ? nstrips - 1 : strip - 1);
+    }
     const int x0 = tx * TW;
     const int ts = strip * a.sh;
     const int te = min(ts + a.sh, L);
-    if (ts >= L || x0 >= a.W) return;
+    if (ts >= L || x0 >= a.W) return;  // uniform across the block
 
     Geo g;
     g.src = a.src;
@@ -322,34 +380,37 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     Meta& m = *reinterpret_cast<Meta*>(sm);
     uint4* pfx = reinterpret_cast<uint4*>(sm + META_BYTES);
     unsigned char* slots = sm + META_BYTES + (size_t)(NC + 1) * 32;
-    const bool use_ring = a.ring && a.dims == 2;
+    const bool use_ring = a.ring && a.dims == 2 && CW == 1;
     T* ring = use_ring ? reinterpret_cast<T*>(slots + (size_t)S * NC * 16 * CW) : nullptr;
     const int M = 2 * r + 2;  // ring rows
-    // the lane's columns cx = lane + 32*j, j < CPL, cover NC <= 32*PPL + 2*127
-    constexpr int CPL = PPL + 8;
+    // the thread's columns cx = tid + NT*j, j < CPL, cover NC <= TW + 2*127
+    constexpr int CPL = PPL + 2;
 
-    load_levels(m, a.desc, a.fixed_shift);
-    if (lane < MAX_SLOTS) {
-        m.key[lane] = lane == 0 ? 0u : KEY_NONE;
-        m.stamp[lane] = lane == 0 ? 0xFFFFFFFFu : 0u;
-        m.pin[lane] = 0;
+    OpCounters oc;
+    oc.reset();
+    const long long t_tile0 = clock64();
+    oc.mark();
+    if (warp == 0) {
+        load_levels(m, a.desc, a.fixed_shift);
+        slots_reset(m);
     }
-    __syncwarp();
-    rehash(m, S);
     if (use_ring) {  // stage input rows ts-r-1 .. ts+r
         for (int u = ts - r - 1; u <= ts + r; ++u) {
             const T* row = reinterpret_cast<const T*>(a.src + (size_t)clampi(u, 0, L - 1) * a.s_row);
             T* dst = ring + (size_t)ring_idx(u, M) * NC;
-#pragma unroll
-            for (int j = 0; j < CPL; ++j) {
-                const int cx = lane + 32 * j;
-                if (cx < NC) dst[cx] = __ldg(row + clampi(x0 - r + cx, 0, a.W - 1));
-            }
+            for (int cx = tid; cx < NC; cx += NT) dst[cx] = __ldg(row + clampi(x0 - r + cx, 0, a.W - 1));
         }
-        __syncwarp();
     }
-    build_slot<T, CW>(a, g, m, slots, NC, x0, ts, 0, 0u, ring);
-    __syncwarp();
+    __syncthreads();
+    if (tid == 0) {
+        m.nbuild = 1;
+        m.build_slot[0] = 0;
+        m.build_key[0] = 0;
+    }
+    __syncthreads();
+    build_slots<T, CW>(a, g, m, slots, NC, x0, ts, ring);
+    __syncthreads();
+    if (tid == 0) m.nbuild = 0;
 
     // 2D: the entering (and, without the ring, the leaving) values of the next
     // step are loaded one step ahead, so their latency hides behind the walk.
@@ -361,7 +422,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         const T* rout = reinterpret_cast<const T*>(a.src + (size_t)to * a.s_row);
 #pragma unroll
         for (int j = 0; j < CPL; ++j) {
-            const int cx = lane + 32 * j;
+            const int cx = tid + NT * j;
             if (cx < NC) {
                 const int gx = clampi(x0 - r + cx, 0, a.W - 1);
                 nin[j] = __ldg(rin + gx);
@@ -370,9 +431,10 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         }
     };
     prefetch(ts + 1);
+    oc.lap(CNT_CYC_INIT);
 
-    // cost model in warp instructions: one shared prefix vs direct n-column sums
-    const int prefix_cost = ((NC + 31) >> 5) * (CW == 1 ? 31 : 24) + 120;
+    // cost model (per block): one shared prefix of a node vs direct n-column sums
+    const int prefix_cost = ((NC + NT - 1) / NT) * (CW == 1 ? 31 : 24) + 300;
     const int direct_cost = n * (CW == 1 ? 17 : 10);
     uint32_t pass_id = 0;
 
@@ -381,25 +443,48 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         if (t > ts) {
             const int to = clampi(t - r - 1, 0, L - 1);
             const int ti = clampi(t + r, 0, L - 1);
-            if (a.dims == 2) {
+            if (a.dims == 2 && CW == 1) {
                 T* rin = use_ring ? ring + (size_t)ring_idx(t + r, M) * NC : nullptr;
                 const T* rout = use_ring ? ring + (size_t)ring_idx(t - r - 1, M) * NC : nullptr;
+                // root level: each of the thread's column records is read,
+                // changed by the leaving and entering values, and written back;
+                // all loads are issued before any store
+                uint32_t vo[CPL], vi[CPL];
+                uint4 rec[CPL];
 #pragma unroll
                 for (int j = 0; j < CPL; ++j) {
-                    const int cx = lane + 32 * j;
+                    const int cx = tid + NT * j;
                     if (cx < NC) {
-                        const uint32_t vi = nin[j];
-                        const uint32_t vo = use_ring ? (uint32_t)rout[cx] : nout[j];
-                        if (use_ring) rin[cx] = (T)vi;
-                        if (vo != vi) {
-                            column_update<CW>(m, slots, NC, cx, vo, -1);
-                            column_update<CW>(m, slots, NC, cx, vi, +1);
+                        vi[j] = nin[j];
+                        vo[j] = use_ring ? (uint32_t)rout[cx] : nout[j];
+                        rec[j] = reinterpret_cast<const uint4*>(slots)[cx];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) {
+                    const int cx = tid + NT * j;
+                    if (cx < NC) {
+                        if (use_ring) rin[cx] = (T)vi[j];
+                        uint32_t dw[4] = {0, 0, 0, 0};
+                        const int co = coarse_of(m, vo[j]), ci = coarse_of(m, vi[j]);
+                        delta_add<1>(dw, co, -1);
+                        delta_add<1>(dw, ci, +1);
+                        rec[j].x += dw[0]; rec[j].y += dw[1]; rec[j].z += dw[2]; rec[j].w += dw[3];
+                        reinterpret_cast<uint4*>(slots)[cx] = rec[j];
+                        if (vo[j] != vi[j]) {
+                            deep_update<CW>(m, slots, NC, cx, vo[j], co, -1);
+                            deep_update<CW>(m, slots, NC, cx, vi[j], ci, +1);
                         }
                     }
                 }
             } else if (to != ti) {
-                for (int cx = lane; cx < NC; cx += 32) {
+                // n leaving and n entering values per column (3D slab); the
+                // root deltas are accumulated in registers and applied once
+                for (int cx = tid; cx < NC; cx += NT) {
                     const int gx = clampi(x0 - r + cx, 0, a.W - 1);
+                    uint32_t dw[4 * CW];
+#pragma unroll
+                    for (int k = 0; k < 4 * CW; ++k) dw[k] = 0;
                     for (int i = 0; i < g.layer; i += 4) {
                         uint32_t vo[4], vi[4];
 #pragma unroll
@@ -411,15 +496,23 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
                             if (i + k < g.layer && vo[k] != vi[k]) {
-                                column_update<CW>(m, slots, NC, cx, vo[k], -1);
-                                column_update<CW>(m, slots, NC, cx, vi[k], +1);
+                                const int co = coarse_of(m, vo[k]), ci = coarse_of(m, vi[k]);
+                                delta_add<CW>(dw, co, -1);
+                                delta_add<CW>(dw, ci, +1);
+                                deep_update<CW>(m, slots, NC, cx, vo[k], co, -1);
+                                deep_update<CW>(m, slots, NC, cx, vi[k], ci, +1);
                             }
                     }
+                    uint32_t* rw = reinterpret_cast<uint32_t*>(slots + (size_t)cx * 16 * CW);
+#pragma unroll
+                    for (int k = 0; k < 4 * CW; ++k) rw[k] += dw[k];
                 }
             }
-            __syncwarp();
             prefetch(t + 1);
+            __syncthreads();
         }
+        oc.lap(CNT_CYC_COLUMNS);
+        oc.add(CNT_ROWS, 1);
 
         // ---- level walk for the TW outputs at walk position t ----
         uint32_t K[PPL], pre[PPL], val[PPL];
@@ -431,20 +524,18 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
             pre[k] = 0;
             val[k] = 0;
             cbin[k] = 0;
-            pend[k] = x0 + lane + 32 * k < a.W;
+            pend[k] = x0 + tid + NT * k < a.W;
         }
         for (int level = 0; level < 6; ++level) {
             bool anyp = false;
 #pragma unroll
             for (int k = 0; k < PPL; ++k) anyp |= pend[k];
-            if (!__any_sync(0xffffffffu, anyp)) break;
+            if (!__syncthreads_or(anyp)) break;
 
-            uint32_t key[PPL];
             int slot[PPL], dig[PPL];
             bool todo[PPL];
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
-                key[k] = level == 0 ? 0u : node_key(level, cbin[k], pre[k]);
                 todo[k] = pend[k];
                 dig[k] = 0;
                 slot[k] = -1;
@@ -453,77 +544,87 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                 bool anyt = false;
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) anyt |= todo[k];
-                if (!__any_sync(0xffffffffu, anyt)) break;
-                if (guard > 32 * PPL + 1) {  // cannot happen: every round settles >= 1 node
-                    if (lane == 0) set_error(a.err, DEV_SLOT_OVERFLOW);
+                if (guard > 0 && !__syncthreads_or(anyt)) break;
+                if (guard > TW + 1) {  // cannot happen: every round settles >= 1 node
+                    if (tid == 0) set_error(a.err, DEV_SLOT_OVERFLOW);
                     break;
                 }
                 ++pass_id;
-                // 1) resident nodes
+                oc.add(CNT_ROUNDS, 1);
+                // 1) resident nodes are pinned for this round, missing ones requested
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) {
                     slot[k] = -1;
                     if (todo[k]) {
-                        slot[k] = level == 0 ? 0 : slot_lookup(m, key[k]);
+                        slot[k] = level == 0 ? 0 : slot_lookup(m, level, cbin[k], pre[k]);
                         if (slot[k] > 0) m.pin[slot[k]] = pass_id;
+                        if (slot[k] < 0) request_node(m, node_key(level, cbin[k], pre[k]));
                     }
                 }
-                __syncwarp();
-                // 2) install missing nodes while unpinned slots remain
-                for (;;) {
-                    int mk = -1;
-#pragma unroll
-                    for (int k = PPL - 1; k >= 0; --k)
-                        if (todo[k] && slot[k] < 0) mk = k;
-                    const unsigned miss = __ballot_sync(0xffffffffu, mk >= 0);
-                    if (!miss) break;
-                    const int leader = __ffs(miss) - 1;
-                    uint32_t mykey = 0;
-#pragma unroll
-                    for (int k = 0; k < PPL; ++k)
-                        if (k == mk) mykey = key[k];
-                    const uint32_t nk = __shfl_sync(0xffffffffu, mykey, leader);
-                    uint32_t cand = 0xFFFFFFFFu;
-                    if (lane > 0 && lane < S && m.pin[lane] != pass_id)
-                        cand = (m.stamp[lane] << 5) | (uint32_t)lane;
-                    cand = __reduce_min_sync(0xffffffffu, cand);
-                    if (cand == 0xFFFFFFFFu) break;  // every slot is in use this round
-                    const int victim = (int)(cand & 31u);
-                    __syncwarp();
-                    if (lane == 0) {
-                        m.key[victim] = nk;
-                        m.pin[victim] = pass_id;
-                        m.stamp[victim] = stampv;
+                __syncthreads();
+                oc.lap(CNT_CYC_RESOLVE);
+                // 2) warp 0 gives unpinned slots (least recently used first) to
+                //    the requested nodes; the block builds them
+                const uint32_t nreq = m.nreq;
+                if (nreq) {
+                    if (warp == 0) {
+                        const uint32_t nr = min(nreq, (uint32_t)REQ_MAX);
+                        uint32_t nb = 0;
+                        for (uint32_t i = 0; i < nr; ++i) {
+                            uint32_t cand = 0xFFFFFFFFu;
+                            if (lane > 0 && lane < S && m.pin[lane] != pass_id)
+                                cand = (m.stamp[lane] << 5) | (uint32_t)lane;
+                            cand = __reduce_min_sync(0xffffffffu, cand);
+                            if (cand == 0xFFFFFFFFu) break;  // every slot is in use this round
+                            const int victim = (int)(cand & 31u);
+                            slot_assign(m, S, victim, m.req[i]);
+                            if (lane == 0) {
+                                m.pin[victim] = pass_id;
+                                m.stamp[victim] = stampv;
+                                m.build_slot[nb] = (uint32_t)victim;
+                                m.build_key[nb] = m.req[i];
+                            }
+                            ++nb;
+                            __syncwarp();
+                        }
+                        for (int i = lane; i < PREQ_SIZE; i += 32) m.preq[i] = KEY_NONE;
+                        if (lane == 0) m.nbuild = nb;  // m.nreq is cleared after the round's last barrier
                     }
-                    __syncwarp();
-                    rehash(m, S);
-                    build_slot<T, CW>(a, g, m, slots, NC, x0, t, victim, nk, ring);
+                    __syncthreads();
+                    build_slots<T, CW>(a, g, m, slots, NC, x0, t, ring);
+                    oc.add(CNT_INSTALLS, m.nbuild);
 #pragma unroll
                     for (int k = 0; k < PPL; ++k)
-                        if (todo[k] && slot[k] < 0 && key[k] == nk) slot[k] = victim;
-                    __syncwarp();
+                        if (todo[k] && slot[k] < 0) {
+                            const int s2 = slot_lookup(m, level, cbin[k], pre[k]);
+                            if (s2 >= 0 && m.pin[s2] == pass_id) slot[k] = s2;
+                        }
                 }
+                oc.lap(CNT_CYC_INSTALL);
                 // 3) window counts of the resolved outputs, then one descent step
                 bool res[PPL];
-                uint32_t used = 0;
                 int nres = 0;
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) {
                     res[k] = todo[k] && slot[k] >= 0;
                     if (res[k]) {
-                        used |= 1u << slot[k];
+                        atomicOr(&m.used, 1u << slot[k]);
+                        atomicMin(&m.span_lo[slot[k]], tid + NT * k);
+                        atomicMax(&m.span_hi[slot[k]], tid + NT * k);
                         ++nres;
                     }
                 }
-                used = __reduce_or_sync(0xffffffffu, used);
-                const int maxres = (int)__reduce_max_sync(0xffffffffu, (unsigned)nres);
+                if (nres) atomicMax(&m.maxres, (unsigned)nres);
+                __syncthreads();
+                const uint32_t used = m.used;
                 const int groups = __popc(used);
-                const bool direct = level > 0 && maxres * direct_cost < groups * prefix_cost;
+                const bool direct = level > 0 && (int)m.maxres * direct_cost < groups * prefix_cost;
+                oc.add(direct ? CNT_DIRECT_ROUNDS : CNT_PREFIXES, direct ? 1 : groups);
                 if (direct) {
 #pragma unroll
                     for (int k = 0; k < PPL; ++k) {
                         if (!res[k]) continue;
-                        const int xl = lane + 32 * k;
+                        const int xl = tid + NT * k;
                         const unsigned char* base = slots + (size_t)slot[k] * NC * 16 * CW;
                         uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                         for (int cx = xl; cx < xl + n; ++cx) rec_add<CW>(w, base + (size_t)cx * 16 * CW);
@@ -534,20 +635,12 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                     while (rem) {
                         const int s = __ffs(rem) - 1;
                         rem &= rem - 1;
-                        int lo = 1 << 30, hi = -1;
-#pragma unroll
-                        for (int k = 0; k < PPL; ++k)
-                            if (res[k] && slot[k] == s) {
-                                lo = min(lo, lane + 32 * k);
-                                hi = max(hi, lane + 32 * k);
-                            }
-                        lo = (int)__reduce_min_sync(0xffffffffu, (unsigned)lo);
-                        hi = (int)__reduce_max_sync(0xffffffffu, (unsigned)(hi + 1)) - 1;
-                        slot_prefix<CW>(slots, pfx, NC, s, lo, hi + 2 * r);
+                        const int lo = m.span_lo[s], hi = m.span_hi[s];
+                        block_prefix<CW>(m, slots, pfx, NC, s, lo, hi + 2 * r);
 #pragma unroll
                         for (int k = 0; k < PPL; ++k) {
                             if (!(res[k] && slot[k] == s)) continue;
-                            const int xl = lane + 32 * k;
+                            const int xl = tid + NT * k;
                             const uint4* pa = pfx + 2 * (xl - lo);
                             const uint4* pb = pfx + 2 * (xl - lo + n);
                             const uint4 a0 = pa[0], a1 = pa[1], b0 = pb[0], b1 = pb[1];
@@ -555,7 +648,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                                              b1.x - a1.x, b1.y - a1.y, b1.z - a1.z, b1.w - a1.w};
                             dig[k] = select16(w, K[k]);
                         }
-                        __syncwarp();
+                        __syncthreads();
                     }
                 }
 #pragma unroll
@@ -564,8 +657,20 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                         if (slot[k] > 0) m.stamp[slot[k]] = stampv;
                         todo[k] = false;
                     }
-                __syncwarp();
+                oc.lap(CNT_CYC_WINDOW);
+                __syncthreads();  // everyone has read used / spans
+                if (tid < MAX_SLOTS) {
+                    m.span_lo[tid] = 0x7FFFFFFF;
+                    m.span_hi[tid] = -1;
+                }
+                if (tid == 0) {
+                    m.used = 0;
+                    m.maxres = 0;
+                    m.nreq = 0;
+                }
+                if (!nreq) break;  // no node was missing: every output of this level is settled
             }
+            oc.add(CNT_LEVELS, 1);
             // advance every output one level down its path
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
@@ -595,10 +700,14 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         const uint32_t mask = a.drop_bits > 0 ? ~((1u << a.drop_bits) - 1u) : 0xFFFFFFFFu;
 #pragma unroll
         for (int k = 0; k < PPL; ++k) {
-            const int x = x0 + lane + 32 * k;
+            const int x = x0 + tid + NT * k;
             if (x < a.W) drow[x] = (T)(val[k] & mask);
         }
+        oc.lap(CNT_CYC_ADVANCE);
     }
+    oc.add(CNT_TILES, 1);
+    oc.add(CNT_CYC_TOTAL, (unsigned long long)(clock64() - t_tile0));
+    if (tid == 0) oc.flush();
 }
 
 }  // namespace hrm

@@ -39,7 +39,7 @@ int workspace_for(cudaStream_t st, Workspace** out);
 
 // Planning.
 struct PlanH {
-    int ppl;      // pixels per lane (TW = 32 * ppl)
+    int ppl;      // outputs per thread (TW = BLOCK_THREADS * ppl)
     int sh;       // strip length along the walk axis
     int nslots;   // slots per warp incl. root
     int path;     // 1 = selection network, 2 = histogram

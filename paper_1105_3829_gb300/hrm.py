@@ -16,7 +16,9 @@ import ctypes as C
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "_build", "libhrm.so")
+# HRM_LIB_VARIANT=count loads the instrumented build (_build/count/libhrm.so).
+_VARIANT = os.environ.get("HRM_LIB_VARIANT", "")
+LIB_PATH = os.path.join(PKG, "_build", _VARIANT, "libhrm.so") if _VARIANT else os.path.join(PKG, "_build", "libhrm.so")
 
 HRM_U8, HRM_U16 = 1, 2
 HRM_BORDER_REPLICATE = 0
@@ -76,7 +78,7 @@ SIGNATURES = {
     "hrm_batch_graph_create": (_I, [C.POINTER(hrm_job), _I, _P, C.POINTER(_P)]),
     "hrm_batch_graph_launch": (_I, [_P, _P]),
     "hrm_batch_graph_destroy": (_I, [_P]),
-    "hrm_autotune": (_I, [_I, _I, _I, _I, _I, _I, _U, _P, C.POINTER(hrm_plan)]),
+    "hrm_autotune": (_I, [_I, _I, _I, _I, _I, _I, _U, _P, _S, _S, _P, C.POINTER(hrm_plan)]),
     "hrm_get_plan": (_I, [_I, _I, _I, _I, _I, _I, _U, C.POINTER(hrm_plan)]),
     "hrm_set_plan": (_I, [_I, _I, _I, _I, _I, _I, _U, C.POINTER(hrm_plan)]),
     "hrm_plan_save": (_I, [C.c_char_p]),
@@ -270,10 +272,16 @@ def device_status(stream=None) -> int:
     return check(lib().hrm_device_status(_stream(stream)), "hrm_device_status")
 
 
-def autotune(dtype: int, dims: int, width: int, height: int, depth: int, radius: int,
-             adaptive: bool = False, stream=None) -> hrm_plan:
+def autotune(img, radius: int, adaptive: bool = False, stream=None) -> hrm_plan:
+    """Time candidate plans on ``img`` (a (H, W) or (D, H, W) CUDA tensor) and
+    cache the fastest for this problem class; returns it."""
     p = hrm_plan()
-    check(lib().hrm_autotune(dtype, dims, width, height, depth, radius, HRM_ADAPTIVE if adaptive else 0,
+    es = img.element_size()
+    dims = img.dim()
+    W, H = img.shape[-1], img.shape[-2]
+    D = img.shape[0] if dims == 3 else 1
+    check(lib().hrm_autotune(_dtype_code(img), dims, W, H, D, radius, HRM_ADAPTIVE if adaptive else 0,
+                             img.data_ptr(), img.stride(-2) * es, img.stride(0) * es if dims == 3 else 0,
                              _stream(stream), C.byref(p)), "hrm_autotune")
     return p
 

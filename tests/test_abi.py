@@ -1,0 +1,92 @@
+"""C-ABI checks that need no GPU: libhrm builds and loads, exports every
+function include/hrm.h declares, and rejects bad arguments before touching
+the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1105_3829_gb300 import build, hrm
+    build.build()
+    return hrm.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "hrm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hrm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("hrm_filter2d", "hrm_filter3d", "hrm_submit", "hrm_poll", "hrm_filter_batch",
+                 "hrm_rank_filter2d", "hrm_server_create", "hrm_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    raw = ctypes.CDLL(lib._name)
+    missing = [n for n in declared_functions() if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_1105_3829_gb300 import hrm
+    assert set(declared_functions()) <= set(hrm.SIGNATURES)
+
+
+def test_version_and_error_string(lib):
+    from paper_1105_3829_gb300 import hrm
+    assert hrm.hrm_version() == 100
+    assert isinstance(hrm.last_error(), str)
+
+
+def test_validation_without_device(lib):
+    from paper_1105_3829_gb300 import hrm
+    buf = ctypes.create_string_buffer(1 << 16)
+    src = ctypes.addressof(buf)
+    dst = src + (1 << 15)
+    E = hrm.HRM_EINVAL
+    assert hrm.hrm_filter2d(3, src, 64, dst, 64, 32, 8, 2, 0, 0, None) == E          # dtype
+    assert hrm.hrm_filter2d(1, src, 64, dst, 64, 32, 8, 128, 0, 0, None) == E        # radius
+    assert hrm.hrm_filter2d(1, src, 64, dst, 64, 32, 8, 2, 1, 0, None) == E          # border
+    assert hrm.hrm_filter2d(1, src, 64, dst, 64, 32, 8, 2, 0, 2, None) == E          # flags
+    assert hrm.hrm_filter2d(1, src, 16, dst, 64, 32, 8, 2, 0, 0, None) == E          # pitch
+    assert hrm.hrm_filter2d(1, src, 64, src + 64, 64, 32, 8, 2, 0, 0, None) == E     # overlap
+    assert hrm.hrm_filter2d(2, src + 1, 64, dst, 64, 16, 8, 2, 0, 0, None) == E      # alignment
+    assert hrm.hrm_filter2d(1, 0, 0, 0, 0, 0, 5, 3, 0, 0, None) == hrm.HRM_OK        # empty
+    assert hrm.hrm_filter3d(1, src, 32, 256, dst, 32, 256, 32, 8, 4, 20, 0, 0, None) == E  # radius 3D
+    assert hrm.hrm_filter3d(1, src, 32, 100, dst, 32, 256, 32, 8, 4, 2, 0, 0, None) == E   # slice pitch
+    assert hrm.hrm_rank_filter2d(1, src, 64, dst, 64, 32, 8, 1, 9, 0, 0, None) == E        # rank >= 9
+    assert hrm.hrm_filter2d_lowprec(1, src, 64, dst, 64, 32, 8, 2, 13, None) == E          # drop bits
+    assert "radius" in hrm.last_error() or "bits" in hrm.last_error()
+
+
+def test_plan_cache_roundtrip(lib, tmp_path):
+    from paper_1105_3829_gb300 import hrm
+    p = hrm.hrm_plan(128, 96, 40, 2)
+    hrm.set_plan(2, 2, 4096, 4096, 1, 15, p)
+    path = str(tmp_path / "plans.txt")
+    assert hrm.hrm_plan_save(path.encode()) == 0
+    text = open(path).read()
+    assert "2 2 4096 4096 1 15 0 128 96 40 2" in text
+    open(path, "a").write("1 2 512 512 1 3 0 64 32 20 2\n")
+    assert hrm.hrm_plan_load(path.encode()) == 0
+    bad = hrm.hrm_plan(100, 0, 0, 0)
+    with pytest.raises(hrm.HRMError):
+        hrm.set_plan(1, 2, 10, 10, 1, 3, bad)
+    open(path, "a").write("garbage line\n")
+    assert hrm.hrm_plan_load(path.encode()) == hrm.HRM_EINVAL
+
+
+def test_batch_rejects_malformed_jobs(lib):
+    from paper_1105_3829_gb300 import hrm
+    jobs = (hrm.hrm_job * 1)()
+    assert hrm.hrm_filter_batch(jobs, -1, None) == hrm.HRM_EINVAL
+    assert hrm.hrm_filter_batch(jobs, 0, None) == hrm.HRM_OK

@@ -1,0 +1,107 @@
+"""Batched persistent-kernel form: every job of a mixed batch (dtype, 2D/3D,
+size, radius) must equal its single-image call bit for bit, and the oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hrm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_3829_gb300 import hrm as h
+    h.lib()
+    return h
+
+
+def _rand(shape, dt, seed, hi=None):
+    rng = np.random.default_rng(seed)
+    top = (256 if dt == np.uint8 else 65536) if hi is None else hi
+    return rng.integers(0, top, size=shape).astype(dt)
+
+
+def _single(hrm, t, r, rank=-1, adaptive=False):
+    if t.dim() == 2:
+        if rank >= 0:
+            return hrm.rank_filter2d(t, r, rank, adaptive=adaptive)
+        return hrm.filter2d(t, r, adaptive=adaptive)
+    return hrm.filter3d(t, r, adaptive=adaptive, rank=None if rank < 0 else rank)
+
+
+def mixed_jobs():
+    from paper_1105_3829_gb300 import inputs
+    return [
+        (_rand((100, 300), np.uint8, 1), 3, -1, False),
+        (inputs.xray12_u16(257, 129, seed=3), 1, -1, False),
+        (inputs.xray12_u16(190, 411, seed=4), 2, -1, False),
+        (inputs.xray12_u16(300, 260, seed=5), 15, -1, False),
+        (_rand((64, 70), np.uint16, 6), 0, -1, False),
+        (inputs.lowkey16_u16(120, 200, seed=7), 9, -1, True),
+        (_rand((40, 50), np.uint16, 8, hi=5000), 4, 11, False),
+        (inputs.xray12_volume(18, 20, 64, seed=9), 2, -1, False),
+        (_rand((9, 17, 33), np.uint8, 10), 1, -1, False),
+        (_rand((1, 1), np.uint8, 11), 5, -1, False),
+    ]
+
+
+def test_mixed_batch_matches_single_calls_and_oracle(hrm, oracle):
+    data = mixed_jobs()
+    srcs = [torch.from_numpy(a).cuda() for a, *_ in data]
+    outs = [torch.zeros_like(s) for s in srcs]
+    jobs = [hrm.make_job(s, o, r, rank=rank, adaptive=ad) for s, o, (_, r, rank, ad) in zip(srcs, outs, data)]
+    hrm.filter_batch(jobs)
+    hrm.device_status()
+    torch.cuda.synchronize()
+    for s, o, (a, r, rank, ad) in zip(srcs, outs, data):
+        single = _single(hrm, s, r, rank, ad)
+        torch.cuda.synchronize()
+        got = o.cpu().numpy()
+        np.testing.assert_array_equal(got, single.cpu().numpy())
+        rk = None if rank < 0 else rank
+        exp = oracle.median2d(a, r, rank=rk) if a.ndim == 2 else oracle.median3d(a, r, rank=rk)
+        np.testing.assert_array_equal(got, exp)
+
+
+def test_graph_replay_matches(hrm, oracle):
+    data = mixed_jobs()[:6]
+    srcs = [torch.from_numpy(a).cuda() for a, *_ in data]
+    outs = [torch.zeros_like(s) for s in srcs]
+    jobs = [hrm.make_job(s, o, r, rank=rank, adaptive=ad) for s, o, (_, r, rank, ad) in zip(srcs, outs, data)]
+    g = hrm.BatchGraph(jobs)
+    for rep in range(3):
+        for o in outs:
+            o.zero_()
+        g.launch()
+        torch.cuda.synchronize()
+        for o, (a, r, rank, ad) in zip(outs, data):
+            np.testing.assert_array_equal(o.cpu().numpy(), oracle.median2d(a, r) if r else a)
+    # inputs changed in place are picked up by the next replay (the graph
+    # holds pointers, not data)
+    new = _rand(tuple(srcs[0].shape), np.uint8, 99)
+    srcs[0].copy_(torch.from_numpy(new))
+    g.launch()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(outs[0].cpu().numpy(), oracle.median2d(new, data[0][1]))
+    g.close()
+
+
+def test_octant_volumes_batch(hrm, oracle):
+    """The 3D workload as 8 independent 128^3 volumes in one launch."""
+    from paper_1105_3829_gb300 import inputs
+    vol = inputs.xray12_volume()
+    octs = inputs.octants(vol)
+    srcs = [torch.from_numpy(o).cuda() for o in octs]
+    for r in (1, 3, 7):
+        outs = [torch.zeros_like(s) for s in srcs]
+        hrm.filter_batch([hrm.make_job(s, o, r) for s, o in zip(srcs, outs)])
+        hrm.device_status()
+        rng = np.random.default_rng(r)
+        for s, o, a in zip(srcs, outs, octs):
+            single = hrm.filter3d(s, r)
+            torch.cuda.synchronize()
+            got = o.cpu().numpy()
+            np.testing.assert_array_equal(got, single.cpu().numpy())
+            zs, ys, xs = (rng.integers(0, 128, 40) for _ in range(3))
+            np.testing.assert_array_equal(got[zs, ys, xs], oracle.points(a, r, ys, xs, zs=zs))
