@@ -146,6 +146,28 @@ typedef struct {
 
 int hrm_filter_batch(const hrm_job* jobs, int njobs, void* stream);
 
+/* hrm_filter_batch_noalloc -- the same batched filter, for callers that must
+ * not allocate device memory.  (The paper has no counterpart: this is a
+ * deployment entry point.)  Some callers cannot call cudaMalloc: code that
+ * runs while a stream is being captured into a CUDA graph (an allocation is
+ * not a stream operation and cannot be recorded), frame loops with a hard
+ * latency budget (an allocation may synchronise the device), and programs
+ * whose device memory is handed out by their own pooling allocator, where a
+ * library allocating behind its back breaks the pool's accounting.
+ *
+ * This call allocates nothing: its scratch (job table, tile offsets, level
+ * descriptors, queue counter, error word, pre-pass histograms) is one
+ * file-scope device array of 64 KiB that every GPU loading the library holds
+ * until the process exits.  It takes at most 64 jobs per call and rejects
+ * more with HRM_EINVAL.  The first call on each device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents (the call clears what must start at zero),
+ * so calls whose work overlaps on the GPU -- on different streams, or from
+ * different threads without ordering -- race: serialise them.  Outputs are
+ * bit-identical to hrm_filter_batch.  Other arguments as for hrm_filter_batch. */
+int hrm_filter_batch_noalloc(const hrm_job* jobs, int njobs, void* stream);
+
 /* hrm_batch_graph_* -- capture the batched launch for a FIXED job list into a
  * CUDA graph once and replay it (no host-side planning or per-job launches on
  * replay).  The job list (pointers included) is frozen at create time. */

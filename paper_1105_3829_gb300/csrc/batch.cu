@@ -15,6 +15,7 @@
 #include <cstring>
 #include <mutex>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "runtime.h"
@@ -180,21 +181,58 @@ static void batchdev_free(BatchDev& b) {
     b = BatchDev{};
 }
 
+// A vector that never allocates: fixed capacity, for the no-allocation path.
+template <class T, int N>
+struct FixedVec {
+    T v[N];
+    int n = 0;
+    bool push_back(const T& x) {
+        if (n >= N) return false;
+        v[n++] = x;
+        return true;
+    }
+    size_t size() const { return (size_t)n; }
+    const T* data() const { return v; }
+    T* begin() { return v; }
+    T* end() { return v + n; }
+    const T* begin() const { return v; }
+    const T* end() const { return v + n; }
+    const T& operator[](size_t i) const { return v[i]; }
+    T& back() { return v[n - 1]; }
+};
+
+template <class T>
+struct HeapVec : std::vector<T> {
+    bool push_back(const T& x) {
+        std::vector<T>::push_back(x);
+        return true;
+    }
+};
+
+struct BatchTmp {
+    BatchItem it;
+    double cost;
+};
+
 // Host-side plan of a batch: items in queue order plus the pre-pass list.
-struct BatchPlan {
-    std::vector<BatchItem> items;
-    std::vector<unsigned> offs;
-    std::vector<LevelItem> levels;      // uniform pre-pass items
-    std::vector<int> adaptive;          // indices into levels that need the adaptive pre-pass
-    std::vector<Image> copies;          // radius-0 jobs
+template <template <class> class V>
+struct BatchPlanT {
+    V<BatchItem> items;
+    V<unsigned> offs;
+    V<LevelItem> levels;      // uniform pre-pass items
+    V<int> adaptive;          // indices into levels that need the adaptive pre-pass
+    V<Image> copies;          // radius-0 jobs
+    V<BatchTmp> tmp;          // planning scratch
     size_t smem = 0;
     unsigned total = 0;
 };
+using BatchPlan = BatchPlanT<HeapVec>;
 
-static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, BatchPlan& bp) {
+template <template <class> class V>
+static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, BatchPlanT<V>& bp) {
     const DeviceInfo& di = device_info();
-    struct Tmp { BatchItem it; double cost; };
-    std::vector<Tmp> tmp;
+    using Tmp = BatchTmp;
+    auto& tmp = bp.tmp;
     for (int i = 0; i < njobs; ++i) {
         const hrm_job& jb = jobs[i];
         if (jb.dims != 2 && jb.dims != 3) return fail(HRM_EINVAL, "job dims must be 2 or 3");
@@ -206,7 +244,7 @@ static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, Batch
         const long n = 2L * jb.radius + 1, N = jb.dims == 3 ? n * n * n : n * n;
         if (jb.rank < -1 || jb.rank >= N) return fail(HRM_EINVAL, "job " + std::to_string(i) + ": rank out of range");
         if (jb.radius == 0) {
-            bp.copies.push_back(im);
+            if (!bp.copies.push_back(im)) return fail(HRM_ENOTSUP, "too many jobs");
             continue;
         }
         const bool median = jb.rank < 0 || jb.rank == (N - 1) / 2;
@@ -236,8 +274,8 @@ static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, Batch
                 if (li >= dev.cap) return fail(HRM_ENOTSUP, "too many jobs for the batch buffer");
                 LevelItem L{(const unsigned char*)im.src, im.sp, im.dims == 3 ? im.sslice : 0, im.W, im.H,
                             im.D, es, dev.descs + li, (jb.flags & HRM_ADAPTIVE) ? 1 : 0, 0};
-                bp.levels.push_back(L);
-                if (jb.flags & HRM_ADAPTIVE) bp.adaptive.push_back(li);
+                if (!bp.levels.push_back(L)) return fail(HRM_ENOTSUP, "too many jobs");
+                if ((jb.flags & HRM_ADAPTIVE) && !bp.adaptive.push_back(li)) return fail(HRM_ENOTSUP, "too many jobs");
                 desc = dev.descs + li;
             }
             t.it.kind = ITEM_HIST;
@@ -247,12 +285,19 @@ static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, Batch
             // expensive tiles first: work per tile grows with the strip and the window
             t.cost = (double)p.sh * ((double)BLOCK_THREADS * p.ppl + 2.0 * jb.radius) * (jb.dims == 3 ? n : 1);
         }
-        tmp.push_back(t);
+        if (!tmp.push_back(t)) return fail(HRM_ENOTSUP, "too many jobs");
     }
-    std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp& a, const Tmp& b) { return a.cost > b.cost; });
+    // expensive tiles first (stable; the fixed-capacity path sorts in place)
+    if constexpr (std::is_same<V<int>, HeapVec<int>>::value) {
+        std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp& a, const Tmp& b) { return a.cost > b.cost; });
+    } else {
+        for (int i = 1; i < (int)tmp.size(); ++i)
+            for (int j = i; j > 0 && tmp.begin()[j - 1].cost < tmp.begin()[j].cost; --j)
+                std::swap(tmp.begin()[j - 1], tmp.begin()[j]);
+    }
     if ((int)tmp.size() > dev.cap) return fail(HRM_ENOTSUP, "too many jobs for the batch buffer");
     unsigned off = 0;
-    for (auto& t : tmp) {
+    for (const Tmp& t : tmp) {
         bp.items.push_back(t.it);
         bp.offs.push_back(off);
         off += (unsigned)t.it.job.ntiles;
@@ -266,7 +311,8 @@ cudaError_t launch_levels_adaptive_only(int elem, const void* src, size_t sp, si
                                         int D, LevelDesc* desc, uint32_t* hist, int num_sms, cudaStream_t st);
 
 // Enqueue a planned batch whose tables are already on the device.
-static int enqueue_batch(const BatchPlan& bp, const BatchDev& dev, cudaStream_t st) {
+template <class Plan>
+static int enqueue_batch(const Plan& bp, const BatchDev& dev, cudaStream_t st) {
     const DeviceInfo& di = device_info();
     cudaError_t e;
     for (const Image& im : bp.copies) {
@@ -375,9 +421,90 @@ static int batch_buffers(cudaStream_t st, int need, BatchDev** out) {
     return HRM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batch without allocation (hrm_filter_batch_noalloc): the job table, tile
+// offsets, level descriptors, queue counter, error word and pre-pass
+// histograms live in one file-scope device array instead of cudaMalloc'ed
+// buffers.  In host code `g_noalloc_scratch` names a host-side stand-in, so its
+// device address is fetched with cudaGetSymbolAddress once per device (with
+// that device current) and passed to the kernels.
+
+constexpr int NOALLOC_MAX_JOBS = 64;
+constexpr size_t NOALLOC_SCRATCH_BYTES = 64 * 1024;
+
+constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t NA_ITEMS = 0;
+constexpr size_t NA_OFFS = na_align(NA_ITEMS + sizeof(BatchItem) * NOALLOC_MAX_JOBS);
+constexpr size_t NA_LEVELS = na_align(NA_OFFS + sizeof(unsigned) * (NOALLOC_MAX_JOBS + 1));
+constexpr size_t NA_DESCS = na_align(NA_LEVELS + sizeof(LevelItem) * NOALLOC_MAX_JOBS);
+constexpr size_t NA_COUNTER = na_align(NA_DESCS + sizeof(LevelDesc) * NOALLOC_MAX_JOBS);
+constexpr size_t NA_ERR = NA_COUNTER + 128;
+constexpr size_t NA_HIST = na_align(NA_ERR + 128);
+constexpr size_t NA_END = NA_HIST + sizeof(uint32_t) * 2 * 4096;
+static_assert(NA_END <= NOALLOC_SCRATCH_BYTES, "no-allocation scratch layout exceeds its array");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_na_mu;
+static unsigned char* g_na_addr[64];  // device address of the array, per device ordinal
+
+static int noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(HRM_ENOTSUP, "device ordinal >= 64");
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+        g_na_addr[dev] = (unsigned char*)p;
+    }
+    *out = g_na_addr[dev];
+    return HRM_OK;
+}
+
+template <class T>
+using NAVec = FixedVec<T, NOALLOC_MAX_JOBS + 1>;
+
 }  // namespace hrm
 
 using namespace hrm;
+
+extern "C" int hrm_filter_batch_noalloc(const hrm_job* jobs, int njobs, void* stream) {
+    if (njobs < 0 || (njobs > 0 && !jobs)) return fail(HRM_EINVAL, "bad job list");
+    if (njobs > NOALLOC_MAX_JOBS)
+        return fail(HRM_EINVAL, "hrm_filter_batch_noalloc takes at most 64 jobs per call (got " +
+                                    std::to_string(njobs) + "); split the batch or use hrm_filter_batch");
+    if (njobs == 0) return HRM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* base = nullptr;
+    int rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    BatchDev dev;
+    dev.items = (BatchItem*)(base + NA_ITEMS);
+    dev.offs = (unsigned*)(base + NA_OFFS);
+    dev.litems = (LevelItem*)(base + NA_LEVELS);
+    dev.descs = (LevelDesc*)(base + NA_DESCS);
+    dev.counter = (unsigned*)(base + NA_COUNTER);
+    dev.err = (unsigned*)(base + NA_ERR);
+    dev.hist = (uint32_t*)(base + NA_HIST);
+    dev.cap = NOALLOC_MAX_JOBS;
+    BatchPlanT<NAVec> plan;  // fixed capacity on the stack: no heap or device allocation
+    rc = plan_batch(jobs, njobs, dev, plan);
+    if (rc) return rc;
+    // The array keeps the previous call's contents: the error word is cleared
+    // here, the queue counter and the level descriptors by enqueue_batch.
+    cudaError_t e = cudaMemsetAsync(dev.err, 0, sizeof(unsigned), st);
+    auto up = [&](void* d, const void* h, size_t n) {
+        if (n && e == cudaSuccess) e = cudaMemcpyAsync(d, h, n, cudaMemcpyHostToDevice, st);
+    };
+    up(dev.items, plan.items.data(), sizeof(BatchItem) * plan.items.size());
+    up(dev.offs, plan.offs.data(), sizeof(unsigned) * plan.offs.size());
+    up(dev.litems, plan.levels.data(), sizeof(LevelItem) * plan.levels.size());
+    if (e != cudaSuccess) return cuda_fail(e, "no-allocation batch upload");
+    return enqueue_batch(plan, dev, st);
+}
 
 struct hrm_batch_graph {
     BatchDev dev;

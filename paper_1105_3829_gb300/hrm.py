@@ -75,6 +75,7 @@ SIGNATURES = {
     "hrm_rank_filter3d": (_I, [_I, _P, _S, _S, _P, _S, _S, _I, _I, _I, _I, _L, _I, _U, _P]),
     "hrm_filter2d_lowprec": (_I, [_I, _P, _S, _P, _S, _I, _I, _I, _I, _P]),
     "hrm_filter_batch": (_I, [C.POINTER(hrm_job), _I, _P]),
+    "hrm_filter_batch_noalloc": (_I, [C.POINTER(hrm_job), _I, _P]),
     "hrm_batch_graph_create": (_I, [C.POINTER(hrm_job), _I, _P, C.POINTER(_P)]),
     "hrm_batch_graph_launch": (_I, [_P, _P]),
     "hrm_batch_graph_destroy": (_I, [_P]),
@@ -241,6 +242,13 @@ def make_job(src, dst, radius: int, rank: int = -1, adaptive: bool = False) -> h
 def filter_batch(jobs, stream=None) -> None:
     arr = (hrm_job * len(jobs))(*jobs)
     check(lib().hrm_filter_batch(arr, len(jobs), _stream(stream)), "hrm_filter_batch")
+
+
+def filter_batch_noalloc(jobs, stream=None) -> None:
+    """hrm_filter_batch_noalloc: the batched filter without any device
+    allocation (at most 64 jobs per call; see include/hrm.h)."""
+    arr = (hrm_job * len(jobs))(*jobs)
+    check(lib().hrm_filter_batch_noalloc(arr, len(jobs), _stream(stream)), "hrm_filter_batch_noalloc")
 
 
 class BatchGraph:
