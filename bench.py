@@ -193,6 +193,154 @@ def run_reference(args, ws, rank):
     return 0
 
 
+# ---- secondary workloads (one JSON line each; not the benchmark headline) --------------
+
+def _timed(fn, flush, reps=5, warm=2):
+    """CUDA-event time (ms) of fn() per call, L2 flushed before each call."""
+    import torch
+    for _ in range(warm):
+        fn()
+    out = []
+    for _ in range(reps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return np.array(out)
+
+
+def _line(metric, unit, value, extra, args, hib=True):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+         "higher_is_better": hib, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    d.update(extra)
+    print(json.dumps(d))
+
+
+def run_secondary(args):
+    import torch
+    from __graft_entry__ import build
+    from paper_1105_3829_gb300 import hrm, inputs
+    build()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    reps = max(3, args.steps)
+    if args.workload == "volume3d":
+        vol_np = inputs.xray12_volume()
+        vol = torch.from_numpy(vol_np).to(dev)
+        octs = [torch.from_numpy(o).to(dev) for o in inputs.octants(vol_np)]
+        nvox = vol.numel()
+        res = {}
+        for r in (1, 3, 7):
+            out = torch.empty_like(vol)
+            outs = [torch.empty_like(o) for o in octs]
+            jobs = [hrm.make_job(o, d_, r) for o, d_ in zip(octs, outs)]
+            g = hrm.BatchGraph(jobs)
+            t_single = _timed(lambda: hrm.filter3d(vol, r, out=out), flush, reps)
+            t_batch = _timed(lambda: hrm.filter_batch(jobs), flush, reps)
+            t_graph = _timed(lambda: g.launch(), flush, reps)
+            t_sep = _timed(lambda: [hrm.filter3d(o, r, out=d_) for o, d_ in zip(octs, outs)], flush, reps)
+            g.close()
+            med = lambda t: float(np.median(t))
+            res[str(r)] = {"volume_256_mvox_s": nvox / med(t_single) / 1e3,
+                           "octants_one_launch_mvox_s": nvox / med(t_batch) / 1e3,
+                           "octants_graph_replay_mvox_s": nvox / med(t_graph) / 1e3,
+                           "octants_8_launches_mvox_s": nvox / med(t_sep) / 1e3,
+                           "p50_ms": {"single": med(t_single), "batch": med(t_batch), "graph": med(t_graph),
+                                      "separate": med(t_sep)},
+                           "p99_ms_batch": float(np.percentile(t_batch, 99))}
+        value = float(np.mean([v["octants_one_launch_mvox_s"] for v in res.values()]))
+        _line("3D median, uint16 256^3 as 8 x 128^3 in one launch: output Mvox/s (mean over r=1,3,7)", "Mvox/s",
+              value, {"dtype": "u16", "per_radius": res,
+                      "config": {"workload": "3D median 256^3 uint16 x-ray mixture + 3D low-frequency noise; "
+                                             "8 octant volumes in one persistent launch vs one 256^3 volume vs 8 "
+                                             "launches", "l2": "flushed before every timed call"}}, args)
+    elif args.workload in ("lowkey2d", "u8small"):
+        if args.workload == "lowkey2d":
+            img_np, radii, dt = inputs.lowkey16_u16(), (15, 50), "u16"
+        else:
+            img_np, radii, dt = inputs.uniform_u8(), (3,), "u8"
+        img = torch.from_numpy(img_np).to(dev)
+        out = torch.empty_like(img)
+        res = {}
+        for r in radii:
+            for ad in ((False, True) if args.workload == "lowkey2d" else (False,)):
+                t = _timed(lambda: hrm.filter2d(img, r, adaptive=ad, out=out), flush, reps)
+                res["r%d%s" % (r, "_adaptive" if ad else "")] = {
+                    "mpix_s": img.numel() / float(np.median(t)) / 1e3, "p50_ms": float(np.median(t)),
+                    "p99_ms": float(np.percentile(t, 99))}
+        value = float(np.mean([v["mpix_s"] for v in res.values()]))
+        _line("2D median %s: output Mpix/s (mean over cases)" % ("8192^2 uint16 low-key" if dt == "u16" else
+                                                               "512^2 uint8 uniform r=3"),
+              "Mpix/s", value, {"dtype": dt, "cases": res,
+                                "config": {"workload": args.workload, "l2": "flushed before every timed call"}}, args)
+    else:
+        run_serve(args, hrm, inputs, torch, dev)
+    return 0
+
+
+def run_serve(args, hrm, inputs, torch, dev):
+    """Continuous batching (hrm server) vs plain per-image launches on the same
+    Poisson request stream: latency from arrival to result, and throughput."""
+    import threading
+    pool = {"u8": torch.from_numpy(inputs.uniform_u8(4096, 4096)).to(dev),
+            "u16": torch.from_numpy(inputs.xray12_u16(4096, 4096)).to(dev)}
+    arena = torch.empty(16 << 30, dtype=torch.uint8, device=dev)  # the 16 GB admission budget
+    results = {}
+    for rate in [float(x) for x in args.rates.split(",")]:
+        n = int(min(args.requests, rate * 10))
+        reqs = inputs.request_stream(n, rate=rate, seed=inputs.seed_for(5, int(rate)))
+        rng = np.random.default_rng(int(rate))
+        views = []
+        for q in reqs:
+            y0, x0 = rng.integers(0, 4097 - q["h"]), rng.integers(0, 4097 - q["w"])
+            views.append(pool[q["dtype"]][y0:y0 + q["h"], x0:x0 + q["w"]])
+        npx = sum(q["w"] * q["h"] for q in reqs)
+        # (a) server: continuous batching
+        srv = hrm.Server(arena, max_inflight=4096, max_queue=16384)
+        outs = [None] * n
+        tick = [0] * n
+        t0 = time.perf_counter()
+        for i, q in enumerate(reqs):
+            while time.perf_counter() - t0 < q["t"]:
+                pass
+            outs[i] = torch.empty_like(views[i])
+            tick[i] = srv.submit(views[i], outs[i], q["r"])
+        for i in range(n):
+            srv.poll(tick[i], -1)
+        t_srv = time.perf_counter() - t0
+        lat_srv = np.array([srv.latency_us(t) for t in tick]) / 1e3
+        st = srv.stats()
+        srv.close()
+        # (b) plain launches: one hrm_filter2d per request, in arrival order
+        stream = torch.cuda.current_stream()
+        lat_plain = np.zeros(n)
+        t0 = time.perf_counter()
+        for i, q in enumerate(reqs):
+            while time.perf_counter() - t0 < q["t"]:
+                pass
+            o = torch.empty_like(views[i])
+            hrm.filter2d(views[i], q["r"], out=o)
+            stream.synchronize()
+            lat_plain[i] = (time.perf_counter() - t0 - q["t"]) * 1e3
+        t_plain = time.perf_counter() - t0
+        results[str(int(rate))] = {
+            "requests": n, "mpix": npx / 1e6,
+            "server": {"mpix_s": npx / t_srv / 1e6, "p50_ms": float(np.percentile(lat_srv, 50)),
+                       "p99_ms": float(np.percentile(lat_srv, 99)), "waves": int(st.waves),
+                       "bytes_high_water": int(st.bytes_high_water)},
+            "plain": {"mpix_s": npx / t_plain / 1e6, "p50_ms": float(np.percentile(lat_plain, 50)),
+                      "p99_ms": float(np.percentile(lat_plain, 99))}}
+    top = results[max(results, key=float)]
+    _line("serving: output Mpix/s and p50/p99 latency, continuous batching vs plain launches", "Mpix/s",
+          top["server"]["mpix_s"], {"dtype": "u8+u16", "per_rate": results,
+                                    "config": {"workload": "Poisson request stream, side log-uniform 64..4096, "
+                                                           "50% uint8 / 50% uint16, radius 1..50, 16 GB budget",
+                                               "value_is": "server Mpix/s at the highest rate"}}, args)
+
+
 # ---- GPU arm ------------------------------------------------------------------------
 
 def main():
@@ -205,6 +353,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=16.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--workload", default="xray2d",
+                    choices=["xray2d", "volume3d", "lowkey2d", "u8small", "serve"],
+                    help="xray2d (default) is the benchmark workload; the others are the secondary configs")
+    ap.add_argument("--rates", default="100,300,1000,3000,5000", help="serve: Poisson arrival rates (1/s)")
+    ap.add_argument("--requests", type=int, default=10000, help="serve: requests per rate (capped at rate x 10 s)")
     ap.add_argument("--radii", default=",".join(map(str, RADII)),
                     help="comma list; the default is the benchmark workload (profiling runs may narrow it)")
     args = ap.parse_args()
@@ -213,6 +366,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload != "xray2d":
+        return run_secondary(args)
 
     import torch
     from __graft_entry__ import build

@@ -145,11 +145,14 @@ static int strip_length(int W, int lines, int walk, int r, int tw, size_t smem, 
 PlanH default_plan(int dims, int es, int W, int lines, int walk, int r, const DeviceInfo& di) {
     PlanH p{};
     p.es = es;
-    p.path = (dims == 2 && r <= 2) ? 1 : 2;
+    p.path = ((dims == 2 && r <= 2) || (dims == 3 && r == 1)) ? 1 : 2;
     p.cw = counter_width(dims, r);
     p.ppl = 1;  // 128 outputs per tile
-    // shared memory per tile: about three resident tiles (12 warps) per SM
-    const size_t budget = std::min((size_t)di.smem_optin, (size_t)di.smem_per_sm / 3 - 1024);
+    // shared memory per tile: about three resident tiles (12 warps) per SM;
+    // large windows get two, with the extra space spent on cached nodes
+    // (their rebuilds read n rows per column, so avoiding them pays most)
+    const size_t per_sm = (size_t)di.smem_per_sm / (r >= 32 ? 2 : 3) - 1024;
+    const size_t budget = std::min((size_t)di.smem_optin, per_sm);
     size_slots(p, dims, r, budget);
     p.sh = strip_length(W, lines, walk, r, BLOCK_THREADS * p.ppl, plan_smem(p, r), di);
     return p;
@@ -279,6 +282,10 @@ int filter_impl(const Image& im, int r, long rank, unsigned flags, int drop_bits
     if (im.dims == 2 && p.path == 1 && r <= 2 && median && drop_bits == 0) {
         e = launch_sortnet2d(es, r, im.src, im.sp, im.dst, im.dp, im.W, im.H, 32, st);
         return e == cudaSuccess ? HRM_OK : cuda_fail(e, "sortnet launch");
+    }
+    if (im.dims == 3 && p.path == 1 && r == 1 && median && drop_bits == 0 && im.H <= 65535) {
+        e = launch_sortnet3d(es, im.src, im.sp, im.sslice, im.dst, im.dp, im.dslice, im.W, im.H, im.D, 32, st);
+        return e == cudaSuccess ? HRM_OK : cuda_fail(e, "sortnet3d launch");
     }
     Workspace* ws = nullptr;
     int rc = workspace_for(st, &ws);

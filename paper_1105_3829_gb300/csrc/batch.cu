@@ -23,7 +23,7 @@
 
 namespace hrm {
 
-enum ItemKind : int { ITEM_HIST = 0, ITEM_SORT3 = 1, ITEM_SORT5 = 2 };
+enum ItemKind : int { ITEM_HIST = 0, ITEM_SORT3 = 1, ITEM_SORT5 = 2, ITEM_SORT3D = 3 };
 
 struct BatchItem {
     HistJob job;       // tile geometry, plan and rank (selection items use src/dst/pitches/W/H)
@@ -82,6 +82,19 @@ __global__ void batch_minmax(const LevelItem* items, int n) {
 
 __device__ void run_item(const BatchItem& it, int tile, unsigned char* sm) {
     const HistJob& j = it.job;
+    if (it.kind == ITEM_SORT3D) {
+        // warp tiles: 256 columns x one row x rows_per_warp slices
+        const int wt = tile * BLOCK_WARPS + (int)(threadIdx.x >> 5);
+        const int tx = wt % it.tiles_x_s, rest = wt / it.tiles_x_s;
+        const int y = rest % j.H, tz = rest / j.H;
+        if (j.elem == 1)
+            sortnet3d_tile<uint8_t>(j.src, j.s_row, j.s_slice, j.dst, j.d_row, j.d_slice, j.W, j.H, j.D,
+                                    it.rows_per_warp, tx, y, tz);
+        else
+            sortnet3d_tile<uint16_t>(j.src, j.s_row, j.s_slice, j.dst, j.d_row, j.d_slice, j.W, j.H, j.D,
+                                     it.rows_per_warp, tx, y, tz);
+        return;
+    }
     if (it.kind != ITEM_HIST) {
         // a block item holds BLOCK_WARPS selection-network warp tiles
         const int wt = tile * BLOCK_WARPS + (int)(threadIdx.x >> 5);
@@ -267,6 +280,24 @@ static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, Batch
             const int wtiles = t.it.tiles_x_s * ((im.H + 31) / 32);
             h.ntiles = (wtiles + BLOCK_WARPS - 1) / BLOCK_WARPS;
             t.cost = 1.0;
+        } else if (jb.dims == 3 && p.path == 1 && jb.radius == 1 && median) {
+            t.it.kind = ITEM_SORT3D;
+            t.it.rows_per_warp = 32;  // slices per warp tile
+            t.it.tiles_x_s = (im.W + 255) / 256;
+            HistJob& h = t.it.job;
+            h.src = (const unsigned char*)im.src;
+            h.dst = (unsigned char*)im.dst;
+            h.s_row = im.sp;
+            h.s_slice = im.sslice;
+            h.d_row = im.dp;
+            h.d_slice = im.dslice;
+            h.W = im.W;
+            h.H = im.H;
+            h.D = im.D;
+            h.elem = es;
+            const long wtiles = (long)t.it.tiles_x_s * im.H * ((im.D + 31) / 32);
+            h.ntiles = (int)((wtiles + BLOCK_WARPS - 1) / BLOCK_WARPS);
+            t.cost = 2.0;
         } else {
             const LevelDesc* desc = nullptr;
             if (es == 2 || (jb.flags & HRM_ADAPTIVE)) {

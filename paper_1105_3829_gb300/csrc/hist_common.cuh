@@ -61,9 +61,12 @@ struct OpCounters {
 constexpr uint32_t KEY_NONE = 0xFFFFFFFFu;
 constexpr int HASH_SIZE = 64;
 constexpr int MAX_SLOTS = 32;
-constexpr int META_BYTES = 5120;  // per-tile metadata block (see Meta)
-constexpr int REQ_MAX = 256;      // node requests per round
-constexpr int PREQ_SIZE = 128;    // pending-request hash (deduplicates requests)
+constexpr int META_BYTES = 2816;  // per-tile metadata block (see Meta)
+// Node requests recorded per round.  A round installs at most one node per
+// free slot (< MAX_SLOTS), so later requests would wait for the next round
+// anyway; requests that find the tables full are simply retried then.
+constexpr int REQ_MAX = 64;
+constexpr int PREQ_SIZE = 64;     // pending-request hash (deduplicates requests)
 constexpr uint8_t NO_SLOT = 0xFF;
 
 // Per-warp metadata in shared memory.  Resident nodes are found through
@@ -86,16 +89,22 @@ struct Meta {
     // block coordination (one tile per thread block)
     uint32_t preq[PREQ_SIZE];   // pending requests of this round (keys)
     uint32_t req[REQ_MAX];      // distinct requested keys in arrival order
-    uint32_t nreq;
     uint32_t nbuild;
-    uint32_t deferred;          // some requests did not get a slot this round
-    uint32_t used;              // slots used by the outputs resolved this round
+    uint32_t pad2[3];
     uint32_t build_slot[MAX_SLOTS];
     uint32_t build_key[MAX_SLOTS];
-    int32_t span_lo[MAX_SLOTS];
-    int32_t span_hi[MAX_SLOTS];
     uint32_t wtot[8][8];        // per-warp totals of the block prefix scan
-    uint32_t maxres;            // most outputs of one thread resolved this round
+    // Per-round bookkeeping, double-buffered by round parity: round k uses
+    // rs[k & 1] and clears rs[(k + 1) & 1] for round k + 1, so no extra
+    // barrier is needed between one round's reads and the next round's writes.
+    struct Round {
+        uint32_t nreq;          // requests recorded
+        uint32_t used;          // slots used by the outputs resolved this round
+        uint32_t maxres;        // most outputs of one thread resolved this round
+        uint32_t pad;
+        int32_t span_lo[MAX_SLOTS];
+        int32_t span_hi[MAX_SLOTS];
+    } rs[2];
 };
 static_assert(sizeof(Meta) <= META_BYTES, "Meta too large");
 
@@ -153,28 +162,43 @@ __device__ __forceinline__ void slots_reset(Meta& m) {
     reinterpret_cast<uint32_t*>(m.lut2)[lane + 32] = 0xFFFFFFFFu;
 #pragma unroll
     for (int i = lane; i < PREQ_SIZE; i += 32) m.preq[i] = KEY_NONE;
-    m.span_lo[lane] = 0x7FFFFFFF;
-    m.span_hi[lane] = -1;
+    for (int b = 0; b < 2; ++b) {
+        m.rs[b].span_lo[lane] = 0x7FFFFFFF;
+        m.rs[b].span_hi[lane] = -1;
+    }
+    if (lane < 2) {
+        m.rs[lane].nreq = 0;
+        m.rs[lane].used = 0;
+        m.rs[lane].maxres = 0;
+    }
     if (lane == 0) {
         m.ndeep = 0;
-        m.nreq = 0;
         m.nbuild = 0;
-        m.deferred = 0;
-        m.used = 0;
-        m.maxres = 0;
     }
     __syncwarp();
+}
+
+// Clear round buffer b (whole warp).
+__device__ __forceinline__ void round_clear(Meta::Round& rb) {
+    const int lane = threadIdx.x & 31;
+    rb.span_lo[lane] = 0x7FFFFFFF;
+    rb.span_hi[lane] = -1;
+    if (lane == 0) {
+        rb.nreq = 0;
+        rb.used = 0;
+        rb.maxres = 0;
+    }
 }
 
 // Record a missing node for this round; duplicates collapse through a small
 // hash of pending keys.  A request that finds the table full is simply not
 // recorded (its outputs retry next round; the first request always fits).
-__device__ __forceinline__ void request_node(Meta& m, uint32_t key) {
+__device__ __forceinline__ void request_node(Meta& m, Meta::Round& rb, uint32_t key) {
     uint32_t h = hash_of(key) & (PREQ_SIZE - 1);
     for (int i = 0; i < PREQ_SIZE; ++i) {
         const uint32_t prev = atomicCAS(&m.preq[h], KEY_NONE, key);
         if (prev == KEY_NONE) {
-            const uint32_t at = atomicAdd(&m.nreq, 1u);
+            const uint32_t at = atomicAdd(&rb.nreq, 1u);
             if (at < REQ_MAX) m.req[at] = key;
             return;
         }

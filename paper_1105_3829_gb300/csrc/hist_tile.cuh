@@ -257,15 +257,21 @@ __device__ __forceinline__ void deep_update(const Meta& m, unsigned char* slots,
 }
 
 // Block-wide inclusive prefix over columns [lo, hi] of slot s into
-// pfx[1 .. hi-lo+1] (pfx[0] = 0): each thread scans an odd-length chunk of
+// pfx[1 .. hi-lo+1] (pfx[0] = 0).  The scratch holds two planes of
+// (NC+1) uint4 each -- words 0..3 then words 4..7 of every column -- so that
+// consecutive lanes touch consecutive 16-byte granules (no bank conflicts).
+// Each thread scans an odd-length chunk of
 // columns (odd so that a quarter-warp's 16-byte records fall in distinct
 // bank groups), then chunk totals are scanned across lanes and warps.
 template <int CW>
 __device__ void block_prefix(Meta& m, const unsigned char* slots, uint4* pfx, int NC, int s, int lo, int hi) {
+    const int plane = NC + 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nt = blockDim.x;
     const int mcols = hi - lo + 1;
-    const int q = ((mcols + nt - 1) / nt) | 1;
+    // chunks long enough that the first warp covers the whole span: the scan
+    // then runs in one warp, and warps without columns skip it
+    const int q = ((mcols + 31) / 32) | 1;
     const int c_begin = lo + tid * q;
     const int c_end = min(c_begin + q, hi + 1);
     uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -287,20 +293,22 @@ __device__ void block_prefix(Meta& m, const unsigned char* slots, uint4* pfx, in
                 acc[0] += rec[u][0].x; acc[1] += rec[u][0].y; acc[2] += rec[u][0].z; acc[3] += rec[u][0].w;
                 acc[4] += rec[u][CW - 1].x; acc[5] += rec[u][CW - 1].y; acc[6] += rec[u][CW - 1].z; acc[7] += rec[u][CW - 1].w;
             }
-            uint4* p = pfx + 2 * (c0 + u - lo + 1);
-            p[0] = make_uint4(acc[0], acc[1], acc[2], acc[3]);
-            p[1] = make_uint4(acc[4], acc[5], acc[6], acc[7]);
+            const int e = c0 + u - lo + 1;
+            pfx[e] = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+            pfx[plane + e] = make_uint4(acc[4], acc[5], acc[6], acc[7]);
         }
     }
     uint32_t inc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) inc[k] = acc[k];
+    if (lo + (tid - lane) * q <= hi) {  // this warp holds columns (uniform per warp)
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
+        for (int off = 1; off < 32; off <<= 1) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint32_t tv = __shfl_up_sync(0xffffffffu, inc[k], off);
-            if (lane >= off) inc[k] += tv;
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t tv = __shfl_up_sync(0xffffffffu, inc[k], off);
+                if (lane >= off) inc[k] += tv;
+            }
         }
     }
     if (lane == 31) {
@@ -315,18 +323,51 @@ __device__ void block_prefix(Meta& m, const unsigned char* slots, uint4* pfx, in
 #pragma unroll
         for (int k = 0; k < 8; ++k) carry[k] += m.wtot[w][k];
     for (int cx = c_begin; cx < c_end; ++cx) {
-        uint4* p = pfx + 2 * (cx - lo + 1);
-        uint4 u0 = p[0], u1 = p[1];
+        const int e = cx - lo + 1;
+        uint4 u0 = pfx[e], u1 = pfx[plane + e];
         u0.x += carry[0]; u0.y += carry[1]; u0.z += carry[2]; u0.w += carry[3];
         u1.x += carry[4]; u1.y += carry[5]; u1.z += carry[6]; u1.w += carry[7];
-        p[0] = u0;
-        p[1] = u1;
+        pfx[e] = u0;
+        pfx[plane + e] = u1;
     }
     if (tid == 0) {
         pfx[0] = make_uint4(0, 0, 0, 0);
-        pfx[1] = make_uint4(0, 0, 0, 0);
+        pfx[plane] = make_uint4(0, 0, 0, 0);
     }
     __syncthreads();
+}
+
+// Record, for the round buffer, which slots this warp's resolved outputs use
+// and the column span of those outputs.  Lanes of a warp nearly always share
+// one or two slots, so the bookkeeping is reduced within the warp first and
+// each distinct slot costs one shared-memory atomic per warp (same-address
+// atomics from all lanes would serialise).
+template <int PPL>
+__device__ __forceinline__ void note_used(Meta::Round& rb, const int (&slot)[PPL], const bool (&res)[PPL],
+                                          int tid, int nt) {
+    uint32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < PPL; ++k)
+        if (res[k]) mine |= 1u << slot[k];
+    uint32_t wused = __reduce_or_sync(0xffffffffu, mine);
+    if (wused && (threadIdx.x & 31) == 0) atomicOr(&rb.used, wused);
+    while (wused) {
+        const int s = __ffs(wused) - 1;
+        wused &= wused - 1;
+        unsigned lo = 0x7FFFFFFFu, hi = 0;
+#pragma unroll
+        for (int k = 0; k < PPL; ++k)
+            if (res[k] && slot[k] == s) {
+                lo = min(lo, (unsigned)(tid + nt * k));
+                hi = max(hi, (unsigned)(tid + nt * k) + 1u);
+            }
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&rb.span_lo[s], (int)lo);
+            atomicMax(&rb.span_hi[s], (int)hi - 1);
+        }
+    }
 }
 
 template <typename T, int PPL, int CW>
@@ -526,12 +567,10 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
             cbin[k] = 0;
             pend[k] = x0 + tid + NT * k < a.W;
         }
-        for (int level = 0; level < 6; ++level) {
-            bool anyp = false;
-#pragma unroll
-            for (int k = 0; k < PPL; ++k) anyp |= pend[k];
-            if (!__syncthreads_or(anyp)) break;
-
+        // every output of a tile row starts at the root: all are pending
+        // exactly when the row has at least one output (x0 < W)
+        bool more = true;
+        for (int level = 0; more && level < 6; ++level) {
             int slot[PPL], dig[PPL];
             bool todo[PPL];
 #pragma unroll
@@ -541,32 +580,47 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                 slot[k] = -1;
             }
             for (int guard = 0;; ++guard) {
-                bool anyt = false;
+                if (guard > 0) {  // a previous round of this level left outputs unresolved
+                    bool anyt = false;
 #pragma unroll
-                for (int k = 0; k < PPL; ++k) anyt |= todo[k];
-                if (guard > 0 && !__syncthreads_or(anyt)) break;
+                    for (int k = 0; k < PPL; ++k) anyt |= todo[k];
+                    if (!__syncthreads_or(anyt)) break;
+                }
                 if (guard > TW + 1) {  // cannot happen: every round settles >= 1 node
                     if (tid == 0) set_error(a.err, DEV_SLOT_OVERFLOW);
                     break;
                 }
                 ++pass_id;
+                Meta::Round& rb = m.rs[pass_id & 1];
                 oc.add(CNT_ROUNDS, 1);
-                // 1) resident nodes are pinned for this round, missing ones requested
+                // 1) resident nodes: pin, record span and use; missing ones: request
+                int nres = 0;
+                bool hit[PPL];
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) {
                     slot[k] = -1;
+                    hit[k] = false;
                     if (todo[k]) {
-                        slot[k] = level == 0 ? 0 : slot_lookup(m, level, cbin[k], pre[k]);
-                        if (slot[k] > 0) m.pin[slot[k]] = pass_id;
-                        if (slot[k] < 0) request_node(m, node_key(level, cbin[k], pre[k]));
+                        const int s = level == 0 ? 0 : slot_lookup(m, level, cbin[k], pre[k]);
+                        slot[k] = s;
+                        if (s >= 0) {
+                            if (s > 0) m.pin[s] = pass_id;
+                            hit[k] = true;
+                            ++nres;
+                        } else {
+                            request_node(m, rb, node_key(level, cbin[k], pre[k]));
+                        }
                     }
                 }
+                note_used<PPL>(rb, slot, hit, tid, NT);
+                // the warp that owns the other round buffer clears it for the next round
+                if (warp == BLOCK_WARPS - 1) round_clear(m.rs[(pass_id + 1) & 1]);
                 __syncthreads();
                 oc.lap(CNT_CYC_RESOLVE);
-                // 2) warp 0 gives unpinned slots (least recently used first) to
-                //    the requested nodes; the block builds them
-                const uint32_t nreq = m.nreq;
+                const uint32_t nreq = rb.nreq;
                 if (nreq) {
+                    // 2) warp 0 gives unpinned slots (least recently used first)
+                    //    to the requested nodes; the block builds them
                     if (warp == 0) {
                         const uint32_t nr = min(nreq, (uint32_t)REQ_MAX);
                         uint32_t nb = 0;
@@ -588,37 +642,45 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                             __syncwarp();
                         }
                         for (int i = lane; i < PREQ_SIZE; i += 32) m.preq[i] = KEY_NONE;
-                        if (lane == 0) m.nbuild = nb;  // m.nreq is cleared after the round's last barrier
+                        if (lane == 0) m.nbuild = nb;
                     }
                     __syncthreads();
                     build_slots<T, CW>(a, g, m, slots, NC, x0, t, ring);
                     oc.add(CNT_INSTALLS, m.nbuild);
+                    bool got[PPL];
 #pragma unroll
-                    for (int k = 0; k < PPL; ++k)
+                    for (int k = 0; k < PPL; ++k) {
+                        got[k] = false;
                         if (todo[k] && slot[k] < 0) {
                             const int s2 = slot_lookup(m, level, cbin[k], pre[k]);
-                            if (s2 >= 0 && m.pin[s2] == pass_id) slot[k] = s2;
+                            if (s2 >= 0 && m.pin[s2] == pass_id) {
+                                slot[k] = s2;
+                                got[k] = true;
+                                ++nres;
+                            }
                         }
+                    }
+                    note_used<PPL>(rb, slot, got, tid, NT);
+                    __syncthreads();  // new records built, all spans recorded
+                }
+                {
+                    const unsigned wmax = __reduce_max_sync(0xffffffffu, (unsigned)nres);
+                    if (wmax && lane == 0) atomicMax(&rb.maxres, wmax);
                 }
                 oc.lap(CNT_CYC_INSTALL);
                 // 3) window counts of the resolved outputs, then one descent step
                 bool res[PPL];
-                int nres = 0;
 #pragma unroll
-                for (int k = 0; k < PPL; ++k) {
-                    res[k] = todo[k] && slot[k] >= 0;
-                    if (res[k]) {
-                        atomicOr(&m.used, 1u << slot[k]);
-                        atomicMin(&m.span_lo[slot[k]], tid + NT * k);
-                        atomicMax(&m.span_hi[slot[k]], tid + NT * k);
-                        ++nres;
-                    }
-                }
-                if (nres) atomicMax(&m.maxres, (unsigned)nres);
-                __syncthreads();
-                const uint32_t used = m.used;
+                for (int k = 0; k < PPL; ++k) res[k] = todo[k] && slot[k] >= 0;
+                const uint32_t used = rb.used;
                 const int groups = __popc(used);
-                const bool direct = level > 0 && (int)m.maxres * direct_cost < groups * prefix_cost;
+                // maxres is complete only after a barrier; the prefix path does not
+                // need it, and the direct path is taken only for levels > 0
+                bool direct = false;
+                if (level > 0 && n * (CW == 1 ? 17 : 10) < groups * prefix_cost) {
+                    __syncthreads();
+                    direct = (int)rb.maxres * direct_cost < groups * prefix_cost;
+                }
                 oc.add(direct ? CNT_DIRECT_ROUNDS : CNT_PREFIXES, direct ? 1 : groups);
                 if (direct) {
 #pragma unroll
@@ -635,20 +697,19 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                     while (rem) {
                         const int s = __ffs(rem) - 1;
                         rem &= rem - 1;
-                        const int lo = m.span_lo[s], hi = m.span_hi[s];
+                        const int lo = rb.span_lo[s], hi = rb.span_hi[s];
                         block_prefix<CW>(m, slots, pfx, NC, s, lo, hi + 2 * r);
 #pragma unroll
                         for (int k = 0; k < PPL; ++k) {
                             if (!(res[k] && slot[k] == s)) continue;
                             const int xl = tid + NT * k;
-                            const uint4* pa = pfx + 2 * (xl - lo);
-                            const uint4* pb = pfx + 2 * (xl - lo + n);
-                            const uint4 a0 = pa[0], a1 = pa[1], b0 = pb[0], b1 = pb[1];
+                            const int ea = xl - lo, eb = xl - lo + n;
+                            const uint4 a0 = pfx[ea], a1 = pfx[NC + 1 + ea], b0 = pfx[eb], b1 = pfx[NC + 1 + eb];
                             uint32_t w[8] = {b0.x - a0.x, b0.y - a0.y, b0.z - a0.z, b0.w - a0.w,
                                              b1.x - a1.x, b1.y - a1.y, b1.z - a1.z, b1.w - a1.w};
                             dig[k] = select16(w, K[k]);
                         }
-                        __syncthreads();
+                        if (rem) __syncthreads();  // the scratch is reused by the next node
                     }
                 }
 #pragma unroll
@@ -658,20 +719,12 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                         todo[k] = false;
                     }
                 oc.lap(CNT_CYC_WINDOW);
-                __syncthreads();  // everyone has read used / spans
-                if (tid < MAX_SLOTS) {
-                    m.span_lo[tid] = 0x7FFFFFFF;
-                    m.span_hi[tid] = -1;
-                }
-                if (tid == 0) {
-                    m.used = 0;
-                    m.maxres = 0;
-                    m.nreq = 0;
-                }
-                if (!nreq) break;  // no node was missing: every output of this level is settled
+                if (!nreq) break;  // nothing was missing: every output of this level is settled
+                __syncthreads();   // end of a round with installs: the next round may rebuild slots
             }
             oc.add(CNT_LEVELS, 1);
             // advance every output one level down its path
+            bool anyp = false;
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
                 if (!pend[k]) continue;
@@ -693,7 +746,11 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                         pend[k] = false;
                     }
                 }
+                anyp |= pend[k];
             }
+            // closes the level: every thread is done with the scratch and the
+            // round buffer, and the block learns whether any output continues
+            more = __syncthreads_or(anyp);
         }
         // ---- store the outputs of walk position t ----
         T* drow = reinterpret_cast<T*>(drow0 + (size_t)t * dstep);

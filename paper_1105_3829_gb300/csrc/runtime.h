@@ -64,6 +64,8 @@ int counter_width(int dims, int r);
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_sortnet2d(int elem, int radius, const void* src, size_t sp, void* dst, size_t dp,
                              int W, int H, int rows_per_warp, cudaStream_t st);
+cudaError_t launch_sortnet3d(int elem, const void* src, size_t sp, size_t ss, void* dst, size_t dp, size_t ds,
+                             int W, int H, int D, int zn, cudaStream_t st);
 cudaError_t launch_hist(const HistJob& job, cudaStream_t st);
 cudaError_t launch_levels(int elem, bool adaptive, const void* src, size_t sp, size_t slice, int W,
                           int H, int D, LevelDesc* desc, uint32_t* hist, int num_sms,

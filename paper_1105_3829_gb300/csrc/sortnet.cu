@@ -12,6 +12,28 @@ __global__ void __launch_bounds__(128) sortnet_kernel(const unsigned char* __res
     else sortnet5x5_tile<T>(src, sp, dst, dp, W, H, rows_per_warp, blockIdx.x, ty);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(128) sortnet3d_kernel(const unsigned char* __restrict__ src, size_t sp, size_t ss,
+                                                        unsigned char* __restrict__ dst, size_t dp, size_t ds, int W,
+                                                        int H, int D, int zn) {
+    // grid: x = 256-column tiles, y = rows, z = groups of 4 slice runs (one per warp)
+    const int tz = blockIdx.z * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    sortnet3d_tile<T>(src, sp, ss, dst, dp, ds, W, H, D, zn, blockIdx.x, blockIdx.y, tz);
+}
+
+cudaError_t launch_sortnet3d(int elem, const void* src, size_t sp, size_t ss, void* dst, size_t dp, size_t ds,
+                             int W, int H, int D, int zn, cudaStream_t st) {
+    if (zn <= 0) zn = 32;
+    const int warps = 4;
+    const int tz = (D + zn - 1) / zn;
+    dim3 grid((W + 255) / 256, H, (tz + warps - 1) / warps);
+    auto s = (const unsigned char*)src;
+    auto d = (unsigned char*)dst;
+    if (elem == 1) sortnet3d_kernel<uint8_t><<<grid, 32 * warps, 0, st>>>(s, sp, ss, d, dp, ds, W, H, D, zn);
+    else sortnet3d_kernel<uint16_t><<<grid, 32 * warps, 0, st>>>(s, sp, ss, d, dp, ds, W, H, D, zn);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 cudaError_t launch_sortnet2d(int elem, int radius, const void* src, size_t sp, void* dst,
                              size_t dp, int W, int H, int rows_per_warp, cudaStream_t st) {

@@ -309,4 +309,134 @@ __device__ void sortnet5x5_tile(const unsigned char* __restrict__ src, size_t sp
     }
 }
 
+// ---------------------------------------------------------------------------
+// 3D, r = 1 (3x3x3).  Per (x, y') column the z-triple (z-1, z, z+1) is sorted
+// once; the 27 window values form a 3 x 9 matrix (rank within the z-triple x
+// the 9 (x, y) columns) with sorted columns.  Sorting each rank-row across the
+// 9 columns keeps the columns sorted; entry (i, j) then has >= (i+1)(j+1)
+// values at or below it and >= (3-i)(9-j) at or above it.  For rank 14 of 27
+// the 13 entries with (i+1)(j+1) <= 14 and (3-i)(9-j) <= 14 remain, 7 entries
+// lie provably below, so the median is the 7th smallest candidate.
+__device__ __forceinline__ uint32_t median27_sorted_cols(uint32_t (&m)[9][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        uint32_t r[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) r[j] = m[j][i];
+        sortnet<9>(r);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) m[j][i] = r[j];
+    }
+    uint32_t cand[13];
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 9; ++j)
+            if ((i + 1) * (j + 1) <= 14 && (3 - i) * (9 - j) <= 14) cand[q++] = m[j][i];
+    sortnet<13>(cand);
+    return cand[6];
+}
+
+template <typename T>
+__device__ __forceinline__ void load8_3d(const unsigned char* src, size_t sp, size_t ss, int W, int H, int D,
+                                        int y, int z, int x, uint32_t (&p)[4]) {
+    load8<T>(src + (size_t)clampi(z, 0, D - 1) * ss, sp, W, clampi(y, 0, H - 1), x, p);
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t load1_3d(const unsigned char* src, size_t sp, size_t ss, int W, int H, int D,
+                                            int y, int z, int x) {
+    return load1<T>(src + (size_t)clampi(z, 0, D - 1) * ss, sp, W, clampi(y, 0, H - 1), x);
+}
+
+// One warp: 256 columns starting at tile_x*256 of row y, slices [z0, z0+zn).
+template <typename T>
+__device__ void sortnet3d_tile(const unsigned char* __restrict__ src, size_t sp, size_t ss,
+                               unsigned char* __restrict__ dst, size_t dp, size_t ds, int W, int H, int D,
+                               int zn, int tile_x, int y, int tile_z) {
+    const int lane = threadIdx.x & 31;
+    const int x = tile_x * 256 + lane * 8;
+    const int z0 = tile_z * zn;
+    if (z0 >= D || y >= H || tile_x * 256 >= W) return;
+    const int z1 = min(z0 + zn, D);
+    const int hx = lane == 0 ? x - 1 : x + 8;
+    // v[t][row][k]: slice z-1+t, row y-1+row, pair k; e[t][row]: halo column (duplicated)
+    uint32_t v[3][3][4], e[3][3];
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            load8_3d<T>(src, sp, ss, W, H, D, y - 1 + q, z0 - 1 + t, x, v[t][q]);
+            e[t][q] = load1_3d<T>(src, sp, ss, W, H, D, y - 1 + q, z0 - 1 + t, hx) * 0x10001u;
+        }
+    for (int z = z0; z < z1; ++z) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            load8_3d<T>(src, sp, ss, W, H, D, y - 1 + q, z + 1, x, v[2][q]);
+            e[2][q] = load1_3d<T>(src, sp, ss, W, H, D, y - 1 + q, z + 1, hx) * 0x10001u;
+        }
+        // sorted z-triples of the lane's columns and of its halo column
+        uint32_t sl[3][4][3], sh[3][3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t a = v[0][q][k], b = v[1][q][k], c = v[2][q][k];
+                uint32_t t1 = vmin2(a, b), t2 = vmax2(a, b);
+                sl[q][k][0] = vmin2(t1, c);
+                uint32_t t3 = vmax2(t1, c);
+                sl[q][k][1] = vmin2(t2, t3);
+                sl[q][k][2] = vmax2(t2, t3);
+            }
+            uint32_t a = e[0][q], b = e[1][q], c = e[2][q];
+            uint32_t t1 = vmin2(a, b), t2 = vmax2(a, b);
+            sh[q][0] = vmin2(t1, c);
+            uint32_t t3 = vmax2(t1, c);
+            sh[q][1] = vmin2(t2, t3);
+            sh[q][2] = vmax2(t2, t3);
+        }
+        uint32_t lp[3][3], rp[3][3];  // neighbour pairs (x-2, x-1) and (x+8, x+9)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                lp[q][i] = __shfl_up_sync(0xffffffffu, sl[q][3][i], 1);
+                rp[q][i] = __shfl_down_sync(0xffffffffu, sl[q][0][i], 1);
+                if (lane == 0) lp[q][i] = sh[q][i];
+                if (lane == 31) rp[q][i] = sh[q][i];
+            }
+        uint32_t o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t m[9][3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const uint32_t P = k == 0 ? lp[q][i] : sl[q][k - 1][i];
+                    const uint32_t C = sl[q][k][i];
+                    const uint32_t N = k == 3 ? rp[q][i] : sl[q][k + 1][i];
+                    m[3 * q + 0][i] = shift1(P, C);
+                    m[3 * q + 1][i] = C;
+                    m[3 * q + 2][i] = shift1(C, N);
+                }
+            o[k] = median27_sorted_cols(m);
+        }
+        store8<T>(dst + (size_t)z * ds, dp, W, y, x, o);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v[0][q][k] = v[1][q][k];
+                v[1][q][k] = v[2][q][k];
+            }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            e[0][q] = e[1][q];
+            e[1][q] = e[2][q];
+        }
+    }
+}
+
 }  // namespace hrm
