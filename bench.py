@@ -134,6 +134,38 @@ def traffic_for(kernel: str):
     return d.get("kernels", {}).get(kernel)
 
 
+# ---- multi-GPU host logic (weak scaling: every rank filters its own image) ----
+
+def rank_seed(rank: int) -> int:
+    """Seed of rank's image: each rank gets a distinct image of the same recipe."""
+    from paper_1105_3829_gb300 import inputs
+    return inputs.seed_for(2, rank)
+
+
+def max_over_ranks(dist, vals, device):
+    """Element-wise max of per-rank floats (the slowest rank sets the time)."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_value(ws: int, nradii: int, npx: int, ms_per_step: float) -> float:
+    """Whole-job Mpix/s: every rank's outputs of one step over the max step time."""
+    return ws * nradii * npx / (ms_per_step * 1e-3) / 1e6
+
+
+def bench_config(ws: int, img=None) -> dict:
+    """The benchmark workload, shared by both arms' JSON lines (with the
+    SHA-256 prefix of rank 0's input image when it is given)."""
+    extra = {} if img is None else {"input_sha256": hashlib.sha256(np.ascontiguousarray(img).tobytes()).hexdigest()[:16]}
+    return extra | {"workload": "2D median, 4096x4096 uint16 12-bit x-ray mixture (0.6 N(800,150) + "
+                        "0.4 N(3000,400), 1% salt/pepper), radii 1/5/15/50, replicate border",
+            "radii": list(RADII), "width": SIDE, "height": SIDE, "parallelism": "dp%d" % ws,
+            "l2": "flushed (512 MiB write) before every launch; ms_per_step is the sum of the "
+                  "launches' CUDA-event times, flushes excluded"}
+
+
 # ---- CPU oracle on a bounded sample ---------------------------------------------
 
 def oracle_sample(img, budget_s: float, radii=RADII):
@@ -145,14 +177,21 @@ def oracle_sample(img, budget_s: float, radii=RADII):
     oracle.build()
     threads = oracle.default_threads()
     rng = np.random.default_rng(12345)
+    # calibration: grow the probe until it takes a measurable time, so the
+    # per-call thread start-up does not dominate the per-point cost
     n0 = 16 * threads
-    cost = 0.0
-    for r in radii:  # calibration
-        ys, xs = rng.integers(0, img.shape[0], n0), rng.integers(0, img.shape[1], n0)
-        t0 = time.perf_counter()
-        oracle.points(img, r, ys, xs, threads=threads)
-        cost += (time.perf_counter() - t0) / n0
-    P = int(max(n0, min(5_000_000, budget_s / max(cost, 1e-9))))
+    while True:
+        spent = 0.0
+        for r in radii:
+            ys, xs = rng.integers(0, img.shape[0], n0), rng.integers(0, img.shape[1], n0)
+            t0 = time.perf_counter()
+            oracle.points(img, r, ys, xs, threads=threads)
+            spent += time.perf_counter() - t0
+        if spent >= min(0.5, budget_s / 8) or n0 >= 1_000_000:
+            break
+        n0 *= 4
+    cost = spent / n0
+    P = int(max(16 * threads, min(20_000_000, budget_s / max(cost, 1e-9))))
     tot_s = 0.0
     for r in radii:
         ys, xs = rng.integers(0, img.shape[0], P), rng.integers(0, img.shape[1], P)
@@ -167,7 +206,7 @@ def run_reference(args, ws, rank):
         return 0
     from paper_1105_3829_gb300 import inputs
     img = inputs.xray12_u16(SIDE, SIDE)
-    step_budget = max(2.0, min(20.0, 90.0 / max(1, args.steps + args.warmup)))
+    step_budget = args.ref_step_seconds or max(2.0, min(20.0, 90.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(img, step_budget / 4, radii=RADII)
     pts, secs = 0, 0.0
@@ -182,8 +221,7 @@ def run_reference(args, ws, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
         "data": "synthetic",
-        "config": {"workload": "2D median, 4096x4096 uint16 12-bit x-ray mixture, radii 1/5/15/50",
-                   "radii": list(RADII), "width": SIDE, "height": SIDE},
+        "config": bench_config(args.gpus, img),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "per step: random output points at each radius, ~%.0f s of CPU work "
                                    "(brute-force gather + Quickselect per point)" % step_budget},
@@ -352,6 +390,8 @@ def main():
     ap.add_argument("--impl", default="hrm", choices=["hrm", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=16.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-step-seconds", type=float, default=None,
+                    help="--impl reference: seconds of oracle work per step (default: 90 s over all steps, 2..20 s)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--workload", default="xray2d",
                     choices=["xray2d", "volume3d", "lowkey2d", "u8small", "serve"],
@@ -384,7 +424,7 @@ def main():
         build()
     dev = torch.device("cuda", local)
 
-    img_np = inputs.xray12_u16(SIDE, SIDE, seed=inputs.seed_for(2, rank))
+    img_np = inputs.xray12_u16(SIDE, SIDE, seed=rank_seed(rank))
     img = torch.from_numpy(img_np).to(dev)
     outs = {r: torch.empty_like(img) for r in RADII}
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -423,10 +463,8 @@ def main():
     times = {r: np.array([ev[k][r][0].elapsed_time(ev[k][r][1]) for k in range(args.steps)]) for r in RADII}
     dev_ms_step = float(sum(times[r].sum() for r in RADII) / args.steps)
     if dist:
-        t = torch.tensor([dev_ms_step, t_wall], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms_step, t_wall = float(t[0]), float(t[1])
-    value = ws * len(RADII) * npx / (dev_ms_step * 1e-3) / 1e6
+        dev_ms_step, t_wall = max_over_ranks(dist, [dev_ms_step, t_wall], dev)
+    value = job_value(ws, len(RADII), npx, dev_ms_step)
 
     # ---- end to end through host buffers (pinned), same workload ----
     if args.no_e2e:
@@ -496,12 +534,7 @@ def report(args, ws, times, dev_ms_step, value, t_wall, e2e_ms, clk, npx, dist, 
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-        "config": {"workload": "2D median, 4096x4096 uint16 12-bit x-ray mixture (0.6 N(800,150) + "
-                               "0.4 N(3000,400), 1% salt/pepper), radii 1/5/15/50, replicate border",
-                   "radii": list(RADII), "width": SIDE, "height": SIDE, "parallelism": "dp%d" % ws,
-                   "l2": "flushed (512 MiB write) before every launch; ms_per_step is the sum of the "
-                         "launches' CUDA-event times, flushes excluded",
-                   "ms_per_step_wall_incl_flush": 1e3 * t_wall / args.steps},
+        "config": dict(bench_config(ws, img_np), ms_per_step_wall_incl_flush=1e3 * t_wall / args.steps),
         "per_radius": per_radius,
         "roofline": {"bound": "hbm", "kernel": kname + " (the hrm_filter2d call: level pre-pass + kernel)",
                      "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,

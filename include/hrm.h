@@ -251,9 +251,10 @@ int hrm_submit(hrm_server* s, const hrm_request* req, uint64_t* ticket);
  * HRM_ECANCELED, or the request's error status.  A ticket that returned
  * HRM_OK is retired and unknown afterwards (HRM_EINVAL). */
 int hrm_poll(hrm_server* s, uint64_t ticket, int timeout_us);
-/* Per-ticket latency in microseconds (submit -> completion event), valid once
- * hrm_poll returned HRM_OK for it and before the next hrm_server_* call that
- * retires it; negative if unknown. */
+/* Per-ticket latency in microseconds (submit -> completion event).  Known
+ * once hrm_poll returned HRM_OK for the ticket; the server remembers the
+ * latencies of the most recent 1,000,000 retired tickets.  Negative for a ticket
+ * that is unknown, still pending, or older than that. */
 double hrm_ticket_latency_us(hrm_server* s, uint64_t ticket);
 int hrm_server_stats_get(hrm_server* s, hrm_server_stats* out);
 /* Stop the loop; pending requests end as HRM_ECANCELED. */

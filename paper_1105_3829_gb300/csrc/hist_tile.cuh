@@ -269,9 +269,9 @@ __device__ void block_prefix(Meta& m, const unsigned char* slots, uint4* pfx, in
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nt = blockDim.x;
     const int mcols = hi - lo + 1;
-    // chunks long enough that the first warp covers the whole span: the scan
-    // then runs in one warp, and warps without columns skip it
-    const int q = ((mcols + 31) / 32) | 1;
+    // odd chunk length: consecutive threads start on different banks; warps
+    // whose threads hold no columns skip the scan
+    const int q = ((mcols + nt - 1) / nt) | 1;
     const int c_begin = lo + tid * q;
     const int c_end = min(c_begin + q, hi + 1);
     uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
