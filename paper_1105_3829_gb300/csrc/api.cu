@@ -148,10 +148,12 @@ PlanH default_plan(int dims, int es, int W, int lines, int walk, int r, const De
     p.path = ((dims == 2 && r <= 2) || (dims == 3 && r == 1)) ? 1 : 2;
     p.cw = counter_width(dims, r);
     p.ppl = 1;  // 128 outputs per tile
-    // shared memory per tile: about three resident tiles (12 warps) per SM;
-    // large windows get two, with the extra space spent on cached nodes
+    // shared memory per tile: small windows get three resident tiles (12
+    // warps) per SM, medium ones four (the kernel is then compiled for 128
+    // registers), large ones two, with the extra space spent on cached nodes
     // (their rebuilds read n rows per column, so avoiding them pays most)
-    const size_t per_sm = (size_t)di.smem_per_sm / (r >= 32 ? 2 : 3) - 1024;
+    const int tiles_per_sm = r >= 32 ? 2 : (r >= 8 ? 4 : 3);
+    const size_t per_sm = (size_t)di.smem_per_sm / tiles_per_sm - 1024;
     const size_t budget = std::min((size_t)di.smem_optin, per_sm);
     size_slots(p, dims, r, budget);
     p.sh = strip_length(W, lines, walk, r, BLOCK_THREADS * p.ppl, plan_smem(p, r), di);

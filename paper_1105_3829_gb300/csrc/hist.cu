@@ -3,18 +3,22 @@
 #include <cuda_runtime.h>
 
 #include "hist_tile.cuh"
+#include "runtime.h"
 
 namespace hrm {
 
-template <typename T, int PPL, int CW>
-__global__ void __launch_bounds__(BLOCK_THREADS, 3) hist_kernel(HistJob job) {
+// MINB = resident tiles per SM the register budget is sized for: 3 (up to
+// 168 registers) by default, 4 (128 registers) when the plan's shared memory
+// lets four tiles share an SM.
+template <typename T, int PPL, int CW, int MINB>
+__global__ void __launch_bounds__(BLOCK_THREADS, MINB) hist_kernel(HistJob job) {
     extern __shared__ __align__(16) unsigned char smem[];
     hist_tile<T, PPL, CW>(job, (int)blockIdx.x, smem);
 }
 
-template <typename T, int PPL, int CW>
+template <typename T, int PPL, int CW, int MINB>
 static cudaError_t launch_one(const HistJob& job, size_t smem, cudaStream_t st) {
-    auto fn = hist_kernel<T, PPL, CW>;
+    auto fn = hist_kernel<T, PPL, CW, MINB>;
     if (smem > 48 * 1024) {  // opt in per launch: the attribute is per device and cheap to set
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -24,16 +28,16 @@ static cudaError_t launch_one(const HistJob& job, size_t smem, cudaStream_t st) 
 }
 
 template <typename T>
-static cudaError_t launch_t(const HistJob& job, size_t smem, cudaStream_t st) {
+static cudaError_t launch_t(const HistJob& job, size_t smem, bool four, cudaStream_t st) {
     if (job.cw == 1) {
         switch (job.ppl) {
-            case 1: return launch_one<T, 1, 1>(job, smem, st);
-            case 2: return launch_one<T, 2, 1>(job, smem, st);
+            case 1: return four ? launch_one<T, 1, 1, 4>(job, smem, st) : launch_one<T, 1, 1, 3>(job, smem, st);
+            case 2: return launch_one<T, 2, 1, 3>(job, smem, st);
         }
     } else if (job.cw == 2) {
         switch (job.ppl) {
-            case 1: return launch_one<T, 1, 2>(job, smem, st);
-            case 2: return launch_one<T, 2, 2>(job, smem, st);
+            case 1: return four ? launch_one<T, 1, 2, 4>(job, smem, st) : launch_one<T, 1, 2, 3>(job, smem, st);
+            case 2: return launch_one<T, 2, 2, 3>(job, smem, st);
         }
     }
     return cudaErrorInvalidValue;
@@ -41,7 +45,9 @@ static cudaError_t launch_t(const HistJob& job, size_t smem, cudaStream_t st) {
 
 cudaError_t launch_hist(const HistJob& job, cudaStream_t st) {
     const size_t smem = hist_smem_bytes(BLOCK_THREADS * job.ppl, job.r, job.nslots, job.cw, job.ring, job.elem);
-    return job.elem == 1 ? launch_t<uint8_t>(job, smem, st) : launch_t<uint16_t>(job, smem, st);
+    const DeviceInfo& di = device_info();
+    const bool four = di.smem_per_sm / (long)(smem + 1024) >= 4;
+    return job.elem == 1 ? launch_t<uint8_t>(job, smem, four, st) : launch_t<uint16_t>(job, smem, four, st);
 }
 
 }  // namespace hrm

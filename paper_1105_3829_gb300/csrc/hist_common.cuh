@@ -61,7 +61,7 @@ struct OpCounters {
 constexpr uint32_t KEY_NONE = 0xFFFFFFFFu;
 constexpr int HASH_SIZE = 64;
 constexpr int MAX_SLOTS = 32;
-constexpr int META_BYTES = 2816;  // per-tile metadata block (see Meta)
+constexpr int META_BYTES = 3072;  // per-tile metadata block (see Meta)
 // Node requests recorded per round.  A round installs at most one node per
 // free slot (< MAX_SLOTS), so later requests would wait for the next round
 // anyway; requests that find the tables full are simply retried then.
@@ -94,9 +94,11 @@ struct Meta {
     uint32_t build_slot[MAX_SLOTS];
     uint32_t build_key[MAX_SLOTS];
     uint32_t wtot[8][8];        // per-warp totals of the block prefix scan
-    // Per-round bookkeeping, double-buffered by round parity: round k uses
-    // rs[k & 1] and clears rs[(k + 1) & 1] for round k + 1, so no extra
-    // barrier is needed between one round's reads and the next round's writes.
+    // Per-round bookkeeping, triple-buffered: round k uses rs[k % 3] and
+    // clears rs[(k + 1) % 3] for round k + 1.  The first round of a level is
+    // resolved before the barrier that closes the previous level, while other
+    // warps may still read rs[(k - 1) % 3]; the buffer being cleared was last
+    // read in round k - 2, before round k - 1's barrier.
     struct Round {
         uint32_t nreq;          // requests recorded
         uint32_t used;          // slots used by the outputs resolved this round
@@ -104,7 +106,7 @@ struct Meta {
         uint32_t pad;
         int32_t span_lo[MAX_SLOTS];
         int32_t span_hi[MAX_SLOTS];
-    } rs[2];
+    } rs[3];
 };
 static_assert(sizeof(Meta) <= META_BYTES, "Meta too large");
 
@@ -162,11 +164,11 @@ __device__ __forceinline__ void slots_reset(Meta& m) {
     reinterpret_cast<uint32_t*>(m.lut2)[lane + 32] = 0xFFFFFFFFu;
 #pragma unroll
     for (int i = lane; i < PREQ_SIZE; i += 32) m.preq[i] = KEY_NONE;
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 3; ++b) {
         m.rs[b].span_lo[lane] = 0x7FFFFFFF;
         m.rs[b].span_hi[lane] = -1;
     }
-    if (lane < 2) {
+    if (lane < 3) {
         m.rs[lane].nreq = 0;
         m.rs[lane].used = 0;
         m.rs[lane].maxres = 0;

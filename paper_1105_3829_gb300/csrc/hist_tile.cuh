@@ -557,8 +557,8 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
 
         // ---- level walk for the TW outputs at walk position t ----
         uint32_t K[PPL], pre[PPL], val[PPL];
-        int cbin[PPL];
-        bool pend[PPL];
+        int cbin[PPL], slot[PPL], dig[PPL];
+        bool pend[PPL], todo[PPL];
 #pragma unroll
         for (int k = 0; k < PPL; ++k) {
             K[k] = a.K;
@@ -567,60 +567,91 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
             cbin[k] = 0;
             pend[k] = x0 + tid + NT * k < a.W;
         }
-        // every output of a tile row starts at the root: all are pending
-        // exactly when the row has at least one output (x0 < W)
-        bool more = true;
-        for (int level = 0; more && level < 6; ++level) {
-            int slot[PPL], dig[PPL];
-            bool todo[PPL];
+        // level 0: the root (slot 0) serves every output of the row, so it
+        // needs no lookup; one prefix over the row's columns
+        {
+            const int hi0 = min(TW, a.W - x0) - 1;
+            block_prefix<CW>(m, slots, pfx, NC, 0, 0, hi0 + 2 * r);
+            oc.add(CNT_ROUNDS, 1);
+            oc.add(CNT_PREFIXES, 1);
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
-                todo[k] = pend[k];
-                dig[k] = 0;
-                slot[k] = -1;
+                if (!pend[k]) continue;
+                const int xl = tid + NT * k;
+                const uint4 a0 = pfx[xl], a1 = pfx[NC + 1 + xl], b0 = pfx[xl + n], b1 = pfx[NC + 1 + xl + n];
+                uint32_t w[8] = {b0.x - a0.x, b0.y - a0.y, b0.z - a0.z, b0.w - a0.w,
+                                 b1.x - a1.x, b1.y - a1.y, b1.z - a1.z, b1.w - a1.w};
+                const int c = select16(w, K[k]);
+                cbin[k] = c;
+                if ((int)m.D[c] <= a.drop_bits) {
+                    val[k] = m.e[c];
+                    pend[k] = false;
+                }
             }
+            oc.add(CNT_LEVELS, 1);
+        }
+        oc.lap(CNT_CYC_WINDOW);
+
+        // One round: pin the resident nodes of the outputs still to do, record
+        // which slots they use and over which columns, request the missing
+        // ones; the last warp clears the round buffer after next.
+        int nres = 0;
+        auto resolve = [&](int level, Meta::Round& rb) {
+            nres = 0;
+            bool hit[PPL];
+#pragma unroll
+            for (int k = 0; k < PPL; ++k) {
+                slot[k] = -1;
+                hit[k] = false;
+                if (todo[k]) {
+                    const int s = slot_lookup(m, level, cbin[k], pre[k]);
+                    slot[k] = s;
+                    if (s >= 0) {
+                        m.pin[s] = pass_id;
+                        hit[k] = true;
+                        ++nres;
+                    } else {
+                        request_node(m, rb, node_key(level, cbin[k], pre[k]));
+                    }
+                }
+            }
+            note_used<PPL>(rb, slot, hit, tid, NT);
+            if (warp == BLOCK_WARPS - 1) round_clear(m.rs[(pass_id + 1) % 3]);
+        };
+        bool anyp = false;
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+            todo[k] = pend[k];
+            anyp |= pend[k];
+        }
+        // the first round of level 1 is resolved before the barrier that
+        // closes level 0 (its prefix scratch is free once that barrier passes)
+        ++pass_id;
+        resolve(1, m.rs[pass_id % 3]);
+        bool more = __syncthreads_or(anyp);
+        oc.lap(CNT_CYC_RESOLVE);
+        for (int level = 1; more && level < 6; ++level) {
             for (int guard = 0;; ++guard) {
                 if (guard > 0) {  // a previous round of this level left outputs unresolved
                     bool anyt = false;
 #pragma unroll
                     for (int k = 0; k < PPL; ++k) anyt |= todo[k];
                     if (!__syncthreads_or(anyt)) break;
-                }
-                if (guard > TW + 1) {  // cannot happen: every round settles >= 1 node
-                    if (tid == 0) set_error(a.err, DEV_SLOT_OVERFLOW);
-                    break;
-                }
-                ++pass_id;
-                Meta::Round& rb = m.rs[pass_id & 1];
-                oc.add(CNT_ROUNDS, 1);
-                // 1) resident nodes: pin, record span and use; missing ones: request
-                int nres = 0;
-                bool hit[PPL];
-#pragma unroll
-                for (int k = 0; k < PPL; ++k) {
-                    slot[k] = -1;
-                    hit[k] = false;
-                    if (todo[k]) {
-                        const int s = level == 0 ? 0 : slot_lookup(m, level, cbin[k], pre[k]);
-                        slot[k] = s;
-                        if (s >= 0) {
-                            if (s > 0) m.pin[s] = pass_id;
-                            hit[k] = true;
-                            ++nres;
-                        } else {
-                            request_node(m, rb, node_key(level, cbin[k], pre[k]));
-                        }
+                    if (guard > TW + 1) {  // cannot happen: every round settles >= 1 node
+                        if (tid == 0) set_error(a.err, DEV_SLOT_OVERFLOW);
+                        break;
                     }
+                    ++pass_id;
+                    resolve(level, m.rs[pass_id % 3]);
+                    __syncthreads();
+                    oc.lap(CNT_CYC_RESOLVE);
                 }
-                note_used<PPL>(rb, slot, hit, tid, NT);
-                // the warp that owns the other round buffer clears it for the next round
-                if (warp == BLOCK_WARPS - 1) round_clear(m.rs[(pass_id + 1) & 1]);
-                __syncthreads();
-                oc.lap(CNT_CYC_RESOLVE);
+                Meta::Round& rb = m.rs[pass_id % 3];
+                oc.add(CNT_ROUNDS, 1);
                 const uint32_t nreq = rb.nreq;
                 if (nreq) {
-                    // 2) warp 0 gives unpinned slots (least recently used first)
-                    //    to the requested nodes; the block builds them
+                    // warp 0 gives unpinned slots (least recently used first)
+                    // to the requested nodes; the block builds them
                     if (warp == 0) {
                         const uint32_t nr = min(nreq, (uint32_t)REQ_MAX);
                         uint32_t nb = 0;
@@ -668,16 +699,15 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                     if (wmax && lane == 0) atomicMax(&rb.maxres, wmax);
                 }
                 oc.lap(CNT_CYC_INSTALL);
-                // 3) window counts of the resolved outputs, then one descent step
+                // window counts of the resolved outputs, then one descent step
                 bool res[PPL];
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) res[k] = todo[k] && slot[k] >= 0;
                 const uint32_t used = rb.used;
                 const int groups = __popc(used);
-                // maxres is complete only after a barrier; the prefix path does not
-                // need it, and the direct path is taken only for levels > 0
+                // maxres is complete only after a barrier; the prefix path does not need it
                 bool direct = false;
-                if (level > 0 && n * (CW == 1 ? 17 : 10) < groups * prefix_cost) {
+                if (n * (CW == 1 ? 17 : 10) < groups * prefix_cost) {
                     __syncthreads();
                     direct = (int)rb.maxres * direct_cost < groups * prefix_cost;
                 }
@@ -715,7 +745,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
 #pragma unroll
                 for (int k = 0; k < PPL; ++k)
                     if (res[k]) {
-                        if (slot[k] > 0) m.stamp[slot[k]] = stampv;
+                        m.stamp[slot[k]] = stampv;
                         todo[k] = false;
                     }
                 oc.lap(CNT_CYC_WINDOW);
@@ -724,33 +754,29 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
             }
             oc.add(CNT_LEVELS, 1);
             // advance every output one level down its path
-            bool anyp = false;
+            anyp = false;
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
                 if (!pend[k]) continue;
-                if (level == 0) {
-                    cbin[k] = dig[k];
-                    const int Dc = (int)m.D[dig[k]];
-                    if (Dc <= a.drop_bits) {
-                        val[k] = m.e[dig[k]];
-                        pend[k] = false;
-                    }
-                } else {
-                    const int Dc = (int)m.D[cbin[k]];
-                    const int top = Dc - 4 * (level - 1);
-                    const int b = min(4, top);
-                    pre[k] = (pre[k] << b) | (uint32_t)dig[k];
-                    const int left = top - b;
-                    if (left <= a.drop_bits) {
-                        val[k] = m.e[cbin[k]] + (pre[k] << left);
-                        pend[k] = false;
-                    }
+                const int Dc = (int)m.D[cbin[k]];
+                const int top = Dc - 4 * (level - 1);
+                const int b = min(4, top);
+                pre[k] = (pre[k] << b) | (uint32_t)dig[k];
+                const int left = top - b;
+                if (left <= a.drop_bits) {
+                    val[k] = m.e[cbin[k]] + (pre[k] << left);
+                    pend[k] = false;
                 }
+                todo[k] = pend[k];
                 anyp |= pend[k];
             }
-            // closes the level: every thread is done with the scratch and the
-            // round buffer, and the block learns whether any output continues
+            oc.lap(CNT_CYC_ADVANCE);
+            // the next level's first round is resolved before the barrier that
+            // closes this level (every thread is then done with the scratch)
+            ++pass_id;
+            resolve(level + 1, m.rs[pass_id % 3]);
             more = __syncthreads_or(anyp);
+            oc.lap(CNT_CYC_RESOLVE);
         }
         // ---- store the outputs of walk position t ----
         T* drow = reinterpret_cast<T*>(drow0 + (size_t)t * dstep);
