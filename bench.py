@@ -36,6 +36,7 @@ METRIC = "output Mpix/s vs radius (uint16 4096^2, bit-exact) and % HBM roofline;
 UNIT = "Mpix/s"
 RADII = (1, 5, 15, 50)
 SIDE = 4096
+SORTNET_MAX_R = 5  # 2D radii served by the selection networks (one launch, no pre-pass)
 
 
 def peaks():
@@ -522,13 +523,13 @@ def report(args, ws, times, dev_ms_step, value, t_wall, e2e_ms, clk, npx, dist, 
             "mpix_s": npx / (p50 * 1e-3) / 1e6,
             "p50_ms": p50, "p99_ms": float(np.percentile(t, 99)),
             "hbm_frac": (4.0 * npx / (p50 * 1e-3) / 1e9) / hbm_gbs,
-            "path": "selection network" if r <= 2 else "levels pre-pass + hierarchical histogram",
+            "path": "selection network" if r <= SORTNET_MAX_R else "levels pre-pass + hierarchical histogram",
         }
     dom = max(RADII, key=lambda r: times[r].mean())
     dom_ms = float(times[dom].mean())
     achieved = 4.0 * npx / (dom_ms * 1e-3) / 1e9
-    kname = "hist2d r=%d" % dom if dom > 2 else "sortnet r=%d" % dom
-    launches_per_step = sum(1 if r <= 2 else 3 for r in RADII)
+    kname = "hist2d r=%d" % dom if dom > SORTNET_MAX_R else "sortnet r=%d" % dom
+    launches_per_step = sum(1 if r <= SORTNET_MAX_R else 3 for r in RADII)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -145,7 +145,7 @@ static int strip_length(int W, int lines, int walk, int r, int tw, size_t smem, 
 PlanH default_plan(int dims, int es, int W, int lines, int walk, int r, const DeviceInfo& di) {
     PlanH p{};
     p.es = es;
-    p.path = ((dims == 2 && r <= 2) || (dims == 3 && r == 1)) ? 1 : 2;
+    p.path = ((dims == 2 && r <= SORTNET_MAX_R2D) || (dims == 3 && r == 1)) ? 1 : 2;
     p.cw = counter_width(dims, r);
     p.ppl = 1;  // 128 outputs per tile
     // shared memory per tile: small windows get three resident tiles (12
@@ -281,7 +281,7 @@ int filter_impl(const Image& im, int r, long rank, unsigned flags, int drop_bits
     const DeviceInfo& di = device_info();
     const PlanH p = resolve_plan(im.dtype, im.dims, im.W, im.H, im.D, r, flags, di, force);
     cudaError_t e;
-    if (im.dims == 2 && p.path == 1 && r <= 2 && median && drop_bits == 0) {
+    if (im.dims == 2 && p.path == 1 && r <= SORTNET_MAX_R2D && median && drop_bits == 0) {
         e = launch_sortnet2d(es, r, im.src, im.sp, im.dst, im.dp, im.W, im.H, 32, st);
         return e == cudaSuccess ? HRM_OK : cuda_fail(e, "sortnet launch");
     }

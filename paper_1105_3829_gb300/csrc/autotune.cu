@@ -1,6 +1,6 @@
 // autotune.cu -- timed search over kernel plans for one problem class.
 //
-// Candidates: the selection network vs the histogram kernel (radius <= 2),
+// Candidates: the selection network vs the histogram kernel (2D radius <= 5),
 // tile width (64/128/256 outputs per warp), shared memory per warp for the
 // node cache (which trades slots against resident warps per SM), and strip
 // length (longer strips amortise the per-tile initial build; shorter strips
@@ -88,7 +88,7 @@ extern "C" int hrm_autotune(int dtype, int dims, int width, int height, int dept
     const long n = 2L * radius + 1;
     const int cw = counter_width(dims, radius);
     if (!rc) {
-        if (dims == 2 && radius <= 2) cands.push_back(hrm_plan{0, 0, 0, 1});
+        if (dims == 2 && radius <= SORTNET_MAX_R2D) cands.push_back(hrm_plan{0, 0, 0, 1});
         const int lines = dims == 3 ? height : 1, walk = dims == 3 ? D : height;
         for (int tw : {BLOCK_THREADS, 2 * BLOCK_THREADS}) {
             if (tw > BLOCK_THREADS && width <= tw / 2) continue;

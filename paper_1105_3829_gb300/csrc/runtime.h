@@ -38,6 +38,9 @@ struct Workspace {
 int workspace_for(cudaStream_t st, Workspace** out);
 
 // Planning.
+// Largest 2D radius served by a selection network (sortnet.cuh).
+constexpr int SORTNET_MAX_R2D = 5;
+
 struct PlanH {
     int ppl;      // outputs per thread (TW = BLOCK_THREADS * ppl)
     int sh;       // strip length along the walk axis

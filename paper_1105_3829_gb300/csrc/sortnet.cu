@@ -1,4 +1,4 @@
-// sortnet.cu -- launch wrapper for the radius 1 / 2 selection networks.
+// sortnet.cu -- launch wrappers for the selection networks (2D radius 1..5, 3D radius 1).
 #include "sortnet.cuh"
 
 namespace hrm {
@@ -9,7 +9,8 @@ __global__ void __launch_bounds__(128) sortnet_kernel(const unsigned char* __res
                                                       int H, int rows_per_warp) {
     const int ty = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (R == 1) sortnet3x3_tile<T>(src, sp, dst, dp, W, H, rows_per_warp, blockIdx.x, ty);
-    else sortnet5x5_tile<T>(src, sp, dst, dp, W, H, rows_per_warp, blockIdx.x, ty);
+    else if (R == 2) sortnet5x5_tile<T>(src, sp, dst, dp, W, H, rows_per_warp, blockIdx.x, ty);
+    else sortnet_wide_tile<T, R>(src, sp, dst, dp, W, H, rows_per_warp, blockIdx.x, ty);
 }
 
 template <typename T>
@@ -41,18 +42,26 @@ cudaError_t launch_sortnet2d(int elem, int radius, const void* src, size_t sp, v
     const int warps = 4;
     dim3 block(32 * warps);
     int tiles_y = (H + rows_per_warp - 1) / rows_per_warp;
-    dim3 grid((W + 255) / 256, (tiles_y + warps - 1) / warps);
+    // columns per warp tile: 256 (r <= 2), else two per output lane
+    const int tw = radius <= 2 ? 256 : 2 * (32 - 2 * ((radius + 1) / 2));
+    dim3 grid((W + tw - 1) / tw, (tiles_y + warps - 1) / warps);
     auto s = (const unsigned char*)src;
     auto d = (unsigned char*)dst;
-    if (radius == 1) {
-        if (elem == 1) sortnet_kernel<uint8_t, 1><<<grid, block, 0, st>>>(s, sp, d, dp, W, H, rows_per_warp);
-        else sortnet_kernel<uint16_t, 1><<<grid, block, 0, st>>>(s, sp, d, dp, W, H, rows_per_warp);
-    } else if (radius == 2) {
-        if (elem == 1) sortnet_kernel<uint8_t, 2><<<grid, block, 0, st>>>(s, sp, d, dp, W, H, rows_per_warp);
-        else sortnet_kernel<uint16_t, 2><<<grid, block, 0, st>>>(s, sp, d, dp, W, H, rows_per_warp);
-    } else {
-        return cudaErrorInvalidValue;
+#define HRM_SORTNET_CASE(RR)                                                                            \
+    case RR:                                                                                            \
+        if (elem == 1) sortnet_kernel<uint8_t, RR><<<grid, block, 0, st>>>(s, sp, d, dp, W, H, rows_per_warp); \
+        else sortnet_kernel<uint16_t, RR><<<grid, block, 0, st>>>(s, sp, d, dp, W, H, rows_per_warp);        \
+        break;
+    switch (radius) {
+        HRM_SORTNET_CASE(1)
+        HRM_SORTNET_CASE(2)
+        HRM_SORTNET_CASE(3)
+        HRM_SORTNET_CASE(4)
+        HRM_SORTNET_CASE(5)
+        default:
+            return cudaErrorInvalidValue;
     }
+#undef HRM_SORTNET_CASE
     return cudaGetLastError();
 }
 

@@ -17,6 +17,10 @@
 //        are provably off-median, and the 7th smallest of the remaining 13 is
 //        the median; the networks are Batcher odd-even merge sorts generated
 //        at compile time and pruned to the outputs actually used.
+// r = 3..5: the same pruning for the general k x k block (k = 2r+1), with
+//        one column pair per lane and the neighbouring columns fetched by
+//        shuffles one rank-row at a time (register footprint ~ the
+//        candidate count: 29, 47, 73 for k = 7, 9, 11).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -26,13 +30,13 @@
 namespace hrm {
 
 // ---------------------------------------------------------------------------
-// Compile-time Batcher odd-even merge sort comparator lists for n <= 32
+// Compile-time Batcher odd-even merge sort comparator lists for n <= 128
 // (generated for the next power of two; comparators touching an index >= n
 // are dropped, which is the same as padding with +infinity).
 struct Net {
     int n = 0;
-    unsigned char a[256] = {};
-    unsigned char b[256] = {};
+    unsigned char a[1536] = {};
+    unsigned char b[1536] = {};
 };
 
 constexpr Net make_net(int N) {
@@ -306,6 +310,136 @@ __device__ void sortnet5x5_tile(const unsigned char* __restrict__ src, size_t sp
             for (int k = 0; k < 4; ++k) rw[t][k] = rw[t + 1][k];
             he[t] = he[t + 1];
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// r = 3..5 (k = 2r+1).  After every column of the k x k block is sorted and
+// then every rank-row is sorted across the k columns, rows and columns are
+// both sorted, so entry (i, j) has at least (i+1)(j+1) entries at or below it
+// and at least (k-i)(k-j) at or above it.  With M = (k^2+1)/2, entries with
+// (i+1)(j+1) > M lie above the median and entries with (k-i)(k-j) > M below
+// it; the remaining candidates of rank-row i are the run j in [jlo(i), jhi(i)]
+// and the median is the (M - #below)-th smallest candidate.
+template <int R>
+struct Wide {
+    static constexpr int K = 2 * R + 1;
+    static constexpr int M = (K * K + 1) / 2;
+    static constexpr int HL = (R + 1) / 2;     // neighbour pairs needed on each side
+    static constexpr int OUTL = 32 - 2 * HL;   // lanes of a warp that produce outputs
+    __host__ __device__ static constexpr int jlo(int i) {
+        int j = 0;
+        while (j < K && (K - i) * (K - j) > M) ++j;
+        return j;
+    }
+    __host__ __device__ static constexpr int jhi(int i) {
+        int j = K - 1;
+        while (j >= 0 && (i + 1) * (j + 1) > M) --j;
+        return j;
+    }
+    static constexpr int ncand() {
+        int c = 0;
+        for (int i = 0; i < K; ++i)
+            if (jhi(i) >= jlo(i)) c += jhi(i) - jlo(i) + 1;
+        return c;
+    }
+    static constexpr int nbelow() {
+        int c = 0;
+        for (int i = 0; i < K; ++i)
+            for (int j = 0; j < K; ++j)
+                if ((K - i) * (K - j) > M) ++c;
+        return c;
+    }
+    static constexpr int NCAND = ncand();
+    static constexpr int SEL = M - nbelow() - 1;  // 0-based index among the sorted candidates
+};
+
+// Two horizontally adjacent values of row y starting at even column c (any
+// c; clamped), as a packed pair.
+template <typename T>
+__device__ __forceinline__ uint32_t loadpair(const unsigned char* src, size_t sp, int W, int y, int c) {
+    const T* row = reinterpret_cast<const T*>(src + (size_t)y * sp);
+    if (c >= 0 && c + 1 < W) {
+        if (sizeof(T) == 2 && (reinterpret_cast<uintptr_t>(row + c) & 3) == 0)
+            return __ldg(reinterpret_cast<const uint32_t*>(row + c));
+        if (sizeof(T) == 1 && (reinterpret_cast<uintptr_t>(row + c) & 1) == 0) {
+            const uint32_t v = __ldg(reinterpret_cast<const unsigned short*>(row + c));
+            return (v & 0xFFu) | ((v >> 8) << 16);
+        }
+    }
+    const uint32_t a = __ldg(row + clampi(c, 0, W - 1));
+    const uint32_t b = __ldg(row + clampi(c + 1, 0, W - 1));
+    return a | (b << 16);
+}
+
+template <typename T>
+__device__ __forceinline__ void storepair(unsigned char* dst, size_t dp, int W, int y, int c, uint32_t v) {
+    T* row = reinterpret_cast<T*>(dst + (size_t)y * dp);
+    if (c + 1 < W) {
+        if (sizeof(T) == 2 && (reinterpret_cast<uintptr_t>(row + c) & 3) == 0) {
+            *reinterpret_cast<uint32_t*>(row + c) = v;
+            return;
+        }
+        if (sizeof(T) == 1 && (reinterpret_cast<uintptr_t>(row + c) & 1) == 0) {
+            *reinterpret_cast<unsigned short*>(row + c) = (unsigned short)((v & 0xFFu) | ((v >> 8) & 0xFF00u));
+            return;
+        }
+    }
+    if (c < W) row[c] = (T)(v & 0xFFFFu);
+    if (c + 1 < W) row[c + 1] = (T)(v >> 16);
+}
+
+// One warp: pairs tile_x*OUTL - HL ... (one aligned column pair per lane; the
+// HL lanes at each edge only supply neighbours), rows [tile_y*rpw, +rpw).
+template <typename T, int R>
+__device__ void sortnet_wide_tile(const unsigned char* __restrict__ src, size_t sp,
+                                  unsigned char* __restrict__ dst, size_t dp, int W, int H,
+                                  int rows_per_warp, int tile_x, int tile_y) {
+    using P = Wide<R>;
+    constexpr int K = P::K, HL = P::HL;
+    const int lane = threadIdx.x & 31;
+    const int c = 2 * (tile_x * P::OUTL + lane - HL);  // first column of the lane's pair
+    const int y0 = tile_y * rows_per_warp;
+    if (y0 >= H || 2 * tile_x * P::OUTL >= W) return;  // uniform across the warp
+    const int y1 = min(y0 + rows_per_warp, H);
+    const bool out_lane = lane >= HL && lane < 32 - HL && c < W;
+
+    uint32_t raw[K];  // rows y-R .. y+R of the lane's pair
+#pragma unroll
+    for (int t = 0; t < K - 1; ++t) raw[t] = loadpair<T>(src, sp, W, clampi(y0 - R + t, 0, H - 1), c);
+    for (int y = y0; y < y1; ++y) {
+        raw[K - 1] = loadpair<T>(src, sp, W, min(y + R, H - 1), c);
+        uint32_t col[K];
+#pragma unroll
+        for (int t = 0; t < K; ++t) col[t] = raw[t];
+        sortnet<K>(col);
+        uint32_t cand[P::NCAND];
+        int q = 0;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            // rank i of the aligned pairs p-HL .. p+HL
+            uint32_t A[2 * HL + 1];
+            A[HL] = col[i];
+#pragma unroll
+            for (int d = 1; d <= HL; ++d) {
+                A[HL - d] = __shfl_up_sync(0xffffffffu, col[i], d);
+                A[HL + d] = __shfl_down_sync(0xffffffffu, col[i], d);
+            }
+            // the k packed columns starting at c-R, c-R+1, ..., c+R
+            uint32_t row[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const int s = j - R + 2 * HL;  // column offset from pair p-HL (>= 0)
+                row[j] = (s & 1) ? shift1(A[s >> 1], A[(s >> 1) + 1]) : A[s >> 1];
+            }
+            sortnet<K>(row);
+#pragma unroll
+            for (int j = P::jlo(i); j <= P::jhi(i); ++j) cand[q++] = row[j];
+        }
+        sortnet<P::NCAND>(cand);
+        if (out_lane) storepair<T>(dst, dp, W, y, c, cand[P::SEL]);
+#pragma unroll
+        for (int t = 0; t < K - 1; ++t) raw[t] = raw[t + 1];
     }
 }
 

@@ -160,3 +160,32 @@ def test_full_size_xray_sampled(hrm, oracle, r):
     ys = np.concatenate([rng.integers(0, 4096, 300), [0, 0, 4095, 4095]])
     xs = np.concatenate([rng.integers(0, 4096, 300), [0, 4095, 0, 4095]])
     np.testing.assert_array_equal(out[ys, xs], oracle.points(img, r, ys, xs))
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("r", [3, 4, 5])
+def test_wide_networks_shapes_and_offsets(hrm, oracle, dt, r):
+    """Radius 3..5 medians take the k x k pruned networks: warp tiles of
+    52-56 columns, ragged edges, images narrower than one tile, and row starts
+    that break the paired loads' alignment."""
+    for shape in [(1, 1), (1, 37), (45, 1), (3, 5), (17, 129), (130, 257), (66, 113)]:
+        img = _rand(shape, dt, 7 * r + sum(shape))
+        np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
+    big = _rand((70, 240), dt, 99 + r)
+    for off in (1, 3):
+        sub = big[:, off:off + 201]
+        out = _host(hrm.filter2d(_dev(big)[:, off:off + 201], r))
+        np.testing.assert_array_equal(out, oracle.median2d(sub, r))
+
+
+@pytest.mark.parametrize("r", [3, 4, 5])
+def test_histogram_path_at_small_radius(hrm, oracle, r):
+    """The histogram kernel still serves radius 3..5 when a plan asks for it."""
+    img = _rand((111, 263), np.uint16, 300 + r, hi=4096)
+    plan = hrm.hrm_plan(128, 0, 0, 2)
+    hrm.set_plan(2, 2, 263, 111, 1, r, plan)
+    try:
+        np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
+        assert hrm.get_plan(2, 2, 263, 111, 1, r).path == 2
+    finally:
+        hrm.set_plan(2, 2, 263, 111, 1, r, hrm.hrm_plan(0, 0, 0, 1))
