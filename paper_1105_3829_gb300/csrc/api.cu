@@ -124,19 +124,28 @@ size_t plan_smem(const PlanH& p, int r) {
 static void size_slots(PlanH& p, int dims, int r, size_t budget) {
     const int tw = BLOCK_THREADS * p.ppl;
     const size_t ring = hist_ring_bytes(tw, r, p.es);
+#ifdef HRM_NO_RING
+    p.ring = 0;
+#else
     p.ring = (dims == 2 && p.cw == 1 && ring * 3 <= budget) ? 1 : 0;
+#endif
     const size_t rest = budget > (p.ring ? ring : 0) ? budget - (p.ring ? ring : 0) : 0;
     p.nslots = std::max(2, std::min(slots_for(tw, r, p.cw, rest), MAX_SLOTS));
 }
 
+// Strip length: about four waves of tiles over the resident tile slots, so
+// that slow tiles (clamped windows at the image edges see noisier medians and
+// more tree nodes) even out, but at least n rows (min 96) so the per-strip
+// start-up -- building the root from n rows and the first cached nodes --
+// stays a small share of a strip.
 static int strip_length(int W, int lines, int walk, int r, int tw, size_t smem, const DeviceInfo& di) {
     int bps = (int)(di.smem_per_sm / (smem + 1024));
     bps = std::max(1, std::min(bps, di.max_blocks_per_sm));
     const long tiles_x = (W + tw - 1) / tw;
-    const long target = (long)di.num_sms * bps * 2;
+    const long target = (long)di.num_sms * bps * 4;
     long sh = (walk * tiles_x * (long)lines + target - 1) / target;
     const long n = 2L * r + 1;
-    sh = std::max(sh, std::min(2 * n, 64L));
+    sh = std::max(sh, std::min(n, 96L));
     sh = std::max(sh, 8L);
     sh = std::min(sh, (long)walk);
     return (int)std::max(1L, sh);
