@@ -151,6 +151,24 @@ static int strip_length(int W, int lines, int walk, int r, int tw, size_t smem, 
     return (int)std::max(1L, sh);
 }
 
+// Edge strips: the r steps at each end of the walk axis, whose windows are
+// clamped, are cut into strips of sh/4 (8 at least) so that the slow tiles
+// near the image corners stay short; the interior keeps strips of sh.
+// Returns the number of strips.
+int strip_layout(int walk, int sh, int r, int* she, int* ne) {
+    *she = 0;
+    *ne = 0;
+    if (sh <= 0) return 0;
+    const int e = std::max(8, sh / 4);
+    const int k = (r + e - 1) / e;
+    if (r >= 8 && e < sh && 2L * k * e + sh <= walk) {
+        *she = e;
+        *ne = k;
+    }
+    const long rest = walk - 2L * *ne * *she;
+    return 2 * *ne + (int)((rest + sh - 1) / sh);
+}
+
 PlanH default_plan(int dims, int es, int W, int lines, int walk, int r, const DeviceInfo& di) {
     PlanH p{};
     p.es = es;
@@ -257,7 +275,8 @@ int make_hist_job(const Image& im, int r, uint32_t K, unsigned flags, int drop_b
     const int walk = im.dims == 3 ? im.D : im.H;
     const int lines = im.dims == 3 ? im.H : 1;
     j.tiles_x = (im.W + tw - 1) / tw;
-    const long nt = (long)j.tiles_x * lines * ((walk + p.sh - 1) / p.sh);
+    const int nstrips = strip_layout(walk, p.sh, r, &j.she, &j.ne);
+    const long nt = (long)j.tiles_x * lines * nstrips;
     if (nt > 0x7FFFFFFFL) return fail(HRM_ENOTSUP, "too many tiles");
     j.ntiles = (int)nt;
     *job = j;

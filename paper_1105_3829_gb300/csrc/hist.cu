@@ -65,4 +65,19 @@ extern "C" int hrm_debug_counters(unsigned long long* out, int n, int reset) {
     }
     return 0;
 }
+
+// Instrumented builds only: restrict the counters to one tile (-1 = all).
+extern "C" int hrm_debug_count_tile(int tile) {
+    return cudaMemcpyToSymbol(hrm::g_hrm_count_tile, &tile, sizeof(int)) == cudaSuccess ? 0 : -3;
+}
+
+// Instrumented builds only: per-tile start/end times (ns) and SM of the last launch.
+extern "C" int hrm_debug_tiles(unsigned long long* t0, unsigned long long* t1, unsigned* sm, int n) {
+    if (n > hrm::CNT_TILE_CAP) n = hrm::CNT_TILE_CAP;
+    cudaDeviceSynchronize();
+    if (cudaMemcpyFromSymbol(t0, hrm::g_hrm_tile_t0, sizeof(unsigned long long) * n) != cudaSuccess) return -3;
+    if (cudaMemcpyFromSymbol(t1, hrm::g_hrm_tile_t1, sizeof(unsigned long long) * n) != cudaSuccess) return -3;
+    if (cudaMemcpyFromSymbol(sm, hrm::g_hrm_tile_sm, sizeof(unsigned) * n) != cudaSuccess) return -3;
+    return 0;
+}
 #endif

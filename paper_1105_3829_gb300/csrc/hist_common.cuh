@@ -36,6 +36,21 @@ enum CountId {
 };
 #ifdef HRM_COUNT_OPS
 static __device__ unsigned long long g_hrm_counters[CNT_NUM];
+static __device__ int g_hrm_count_tile = -1;  // >= 0: only that tile adds to the counters
+// per-tile timeline of the last launch (tile id -> start/end global time, SM)
+constexpr int CNT_TILE_CAP = 1 << 15;
+static __device__ unsigned long long g_hrm_tile_t0[CNT_TILE_CAP], g_hrm_tile_t1[CNT_TILE_CAP];
+static __device__ unsigned g_hrm_tile_sm[CNT_TILE_CAP];
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned sm_id() {
+    unsigned s;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+    return s;
+}
 struct OpCounters {
     unsigned long long v[CNT_NUM];
     long long t0;
@@ -43,18 +58,29 @@ struct OpCounters {
     __device__ void add(int i, unsigned long long x) { v[i] += x; }
     __device__ void mark() { t0 = clock64(); }
     __device__ void lap(int i) { long long t = clock64(); v[i] += (unsigned long long)(t - t0); t0 = t; }
-    __device__ void flush() {
+    __device__ void flush(int tile = -1) {
+        if (g_hrm_count_tile >= 0 && tile != g_hrm_count_tile) return;
         if ((threadIdx.x & 31) == 0)
             for (int i = 0; i < CNT_NUM; ++i) if (v[i]) atomicAdd(&g_hrm_counters[i], v[i]);
     }
+    __device__ void tile(int id, unsigned long long ns0) {
+        if (id >= 0 && id < CNT_TILE_CAP) {
+            g_hrm_tile_t0[id] = ns0;
+            g_hrm_tile_t1[id] = global_ns();
+            g_hrm_tile_sm[id] = sm_id();
+        }
+    }
+    __device__ unsigned long long now_ns() { return global_ns(); }
 };
 #else
 struct OpCounters {
+    __device__ void tile(int, unsigned long long) {}
+    __device__ unsigned long long now_ns() { return 0; }
     __device__ void reset() {}
     __device__ void add(int, unsigned long long) {}
     __device__ void mark() {}
     __device__ void lap(int) {}
-    __device__ void flush() {}
+    __device__ void flush(int = -1) {}
 };
 #endif
 

@@ -54,7 +54,8 @@ struct HistJob {
     int W, H, D;             // D = 1 for 2D
     int dims;                // 2 or 3
     int r;
-    int sh;                  // strip length along the walk axis
+    int sh;                  // strip length along the walk axis (interior strips)
+    int she, ne;             // edge strips: ne strips of she steps at each end of the walk axis
     int tiles_x;             // tiles across x
     int ntiles;
     uint32_t K;              // 1-based target rank
@@ -387,15 +388,27 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         strip = rest / a.H;
     }
     const int L = a.dims == 3 ? a.D : a.H;  // walk-axis length
-    {
-        // Strips at the two ends of the walk axis see clamped windows with
-        // noisier medians (more tree nodes per row): schedule them first.
-        const int nstrips = (L + a.sh - 1) / a.sh;
-        if (nstrips >= 3) strip = strip == 0 ? 0 : (strip == 1 ? nstrips - 1 : strip - 1);
-    }
+    // Steps within r of either end of the walk axis see clamped windows whose
+    // medians are much noisier (more tree nodes per row; near the image
+    // corners several times the work of an interior step).  They come first
+    // (low tile ids start first) in short edge strips, alternating ends;
+    // the interior follows in strips of sh steps.
     const int x0 = tx * TW;
-    const int ts = strip * a.sh;
-    const int te = min(ts + a.sh, L);
+    int ts, te;
+    if (strip < 2 * a.ne) {
+        const int k = strip >> 1;
+        if ((strip & 1) == 0) {
+            ts = k * a.she;
+            te = ts + a.she;
+        } else {
+            te = L - k * a.she;
+            ts = te - a.she;
+        }
+    } else {
+        const int lo = a.ne * a.she;
+        ts = lo + (strip - 2 * a.ne) * a.sh;
+        te = min(ts + a.sh, L - lo);
+    }
     if (ts >= L || x0 >= a.W) return;  // uniform across the block
 
     Geo g;
@@ -429,6 +442,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
 
     OpCounters oc;
     oc.reset();
+    const unsigned long long ns_tile0 = oc.now_ns();
     const long long t_tile0 = clock64();
     oc.mark();
     if (warp == 0) {
@@ -790,7 +804,10 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     }
     oc.add(CNT_TILES, 1);
     oc.add(CNT_CYC_TOTAL, (unsigned long long)(clock64() - t_tile0));
-    if (tid == 0) oc.flush();
+    if (tid == 0) {
+        oc.flush(tile);
+        oc.tile(tile, ns_tile0);
+    }
 }
 
 }  // namespace hrm

@@ -189,3 +189,18 @@ def test_histogram_path_at_small_radius(hrm, oracle, r):
         assert hrm.get_plan(2, 2, 263, 111, 1, r).path == 2
     finally:
         hrm.set_plan(2, 2, 263, 111, 1, r, hrm.hrm_plan(0, 0, 0, 1))
+
+
+@pytest.mark.parametrize("r,H", [(8, 120), (21, 200), (40, 420)])
+def test_edge_strips(hrm, oracle, r, H):
+    """Images tall enough that the rows within r of the top and bottom edges
+    are cut into short edge strips ahead of the interior strips."""
+    from paper_1105_3829_gb300 import inputs
+    img = inputs.xray12_u16(H, 300, seed=60 + r)
+    np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
+    for sh in (24, 40):  # other interior strip lengths (edge strips sh/4, at least 8)
+        hrm.set_plan(2, 2, 300, H, 1, r, hrm.hrm_plan(128, sh, 0, 2))
+        try:
+            np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
+        finally:
+            hrm.set_plan(2, 2, 300, H, 1, r, hrm.hrm_plan(0, 0, 0, 0))

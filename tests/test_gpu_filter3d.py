@@ -86,3 +86,10 @@ def test_full_size_volume_sampled(hrm, oracle):
     rng = np.random.default_rng(3)
     zs, ys, xs = (np.concatenate([rng.integers(0, 256, 200), [0, 255]]) for _ in range(3))
     np.testing.assert_array_equal(out[zs, ys, xs], oracle.points(vol, 3, ys, xs, zs=zs))
+
+
+def test_edge_slabs_along_z(hrm, oracle):
+    """A volume deep enough that the slices within r of both z ends are cut
+    into short edge strips ahead of the interior ones."""
+    vol = _rand((64, 11, 30), np.uint16, 5, hi=4096)
+    np.testing.assert_array_equal(run3d(hrm, vol, 8), oracle.median3d(vol, 8))
