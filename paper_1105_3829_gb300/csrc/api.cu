@@ -152,14 +152,14 @@ static int strip_length(int W, int lines, int walk, int r, int tw, size_t smem, 
 }
 
 // Edge strips: the r steps at each end of the walk axis, whose windows are
-// clamped, are cut into strips of sh/4 (8 at least) so that the slow tiles
-// near the image corners stay short; the interior keeps strips of sh.
-// Returns the number of strips.
+// clamped, are cut into strips of 8 so that the slow tiles near the image
+// corners (their medians move to new tree nodes almost every step) stay
+// short; the interior keeps strips of sh.  Returns the number of strips.
 int strip_layout(int walk, int sh, int r, int* she, int* ne) {
     *she = 0;
     *ne = 0;
     if (sh <= 0) return 0;
-    const int e = std::max(8, sh / 4);
+    const int e = 8;
     const int k = (r + e - 1) / e;
     if (r >= 8 && e < sh && 2L * k * e + sh <= walk) {
         *she = e;
@@ -175,11 +175,10 @@ PlanH default_plan(int dims, int es, int W, int lines, int walk, int r, const De
     p.path = ((dims == 2 && r <= SORTNET_MAX_R2D) || (dims == 3 && r == 1)) ? 1 : 2;
     p.cw = counter_width(dims, r);
     p.ppl = 1;  // 128 outputs per tile
-    // shared memory per tile: small windows get three resident tiles (12
-    // warps) per SM, medium ones four (the kernel is then compiled for 128
-    // registers), large ones two, with the extra space spent on cached nodes
-    // (their rebuilds read n rows per column, so avoiding them pays most)
-    const int tiles_per_sm = r >= 32 ? 2 : (r >= 8 ? 4 : 3);
+    // shared memory per tile: four resident tiles (16 warps, the kernel then
+    // compiled for 128 registers) per SM for medium windows, three for small
+    // and large ones (more cached nodes: rebuilds read n rows per column)
+    const int tiles_per_sm = (r >= 8 && r < 40) ? 4 : 3;
     const size_t per_sm = (size_t)di.smem_per_sm / tiles_per_sm - 1024;
     const size_t budget = std::min((size_t)di.smem_optin, per_sm);
     size_slots(p, dims, r, budget);

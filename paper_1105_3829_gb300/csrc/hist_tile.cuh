@@ -185,39 +185,64 @@ __device__ __forceinline__ int node_digit(const Meta& m, const NodeRange& nr, ui
 // Build the records of m.nbuild new slots at walk position t (whole block):
 // work items (slot, column) are spread over the threads; values come from the
 // shared-memory ring when present (2D), else from global memory with eight
-// loads in flight per thread.
+// loads in flight per thread.  The index arithmetic per value is kept to a
+// clamp and a multiply-add (no division): installs near the image corners,
+// where medians move to new nodes every row, are dominated by this loop.
 template <typename T, int CW>
 __device__ void build_slots(const HistJob& a, const Geo& g, const Meta& m, unsigned char* slots, int NC,
                             int x0, int t, const T* ring) {
     const int r = a.r;
+    const int n = 2 * r + 1;
     const int nb = (int)m.nbuild;
     const int items = nb * NC;
-    const int nv = (2 * r + 1) * g.layer;  // values per column
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int b = it / NC, cx = it - b * NC;
         const NodeRange nr = node_range(m, m.build_key[b]);
         uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (ring) {
             const int M = 2 * r + 2;
+            int idx = ring_idx(t - r, M);
+            const T* col = ring + cx;
 #pragma unroll 4
-            for (int tt = t - r; tt <= t + r; ++tt) {
-                const int d = node_digit(m, nr, (uint32_t)ring[(size_t)ring_idx(tt, M) * NC + cx]);
+            for (int k = 0; k < n; ++k) {
+                const int d = node_digit(m, nr, (uint32_t)col[(size_t)idx * NC]);
                 if (d >= 0) reg_count<CW>(cnt, d);
+                idx = idx + 1 == M ? 0 : idx + 1;
             }
         } else {
-            const int gx = clampi(x0 - r + cx, 0, a.W - 1);
-            for (int q0 = 0; q0 < nv; q0 += 8) {
-                uint32_t v[8];
+            const unsigned char* base = g.src + (size_t)clampi(x0 - r + cx, 0, a.W - 1) * sizeof(T);
+            if (g.layer == 1) {  // 2D: one value per walk step
+                for (int k0 = 0; k0 < n; k0 += 8) {
+                    uint32_t v[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int q = min(q0 + u, nv - 1);
-                    v[u] = geo_ld<T>(g, t - r + q / g.layer, q % g.layer, gx);
+                    for (int u = 0; u < 8; ++u) {
+                        const int tc = clampi(t - r + min(k0 + u, n - 1), 0, g.tmax);
+                        v[u] = __ldg(reinterpret_cast<const T*>(base + (size_t)tc * g.tstride));
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        if (k0 + u >= n) break;
+                        const int d = node_digit(m, nr, v[u]);
+                        if (d >= 0) reg_count<CW>(cnt, d);
+                    }
                 }
+            } else {  // 3D: a slab of `layer` rows per walk step
+                for (int k = 0; k < n; ++k) {
+                    const unsigned char* sl = base + (size_t)clampi(t - r + k, 0, g.tmax) * g.tstride;
+                    for (int i0 = 0; i0 < g.layer; i0 += 8) {
+                        uint32_t v[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (q0 + u >= nv) break;
-                    const int d = node_digit(m, nr, v[u]);
-                    if (d >= 0) reg_count<CW>(cnt, d);
+                        for (int u = 0; u < 8; ++u) {
+                            const int ic = clampi(g.ibase + min(i0 + u, g.layer - 1), 0, g.imax);
+                            v[u] = __ldg(reinterpret_cast<const T*>(sl + (size_t)ic * g.istride));
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            if (i0 + u >= g.layer) break;
+                            const int d = node_digit(m, nr, v[u]);
+                            if (d >= 0) reg_count<CW>(cnt, d);
+                        }
+                    }
                 }
             }
         }

@@ -198,7 +198,7 @@ def test_edge_strips(hrm, oracle, r, H):
     from paper_1105_3829_gb300 import inputs
     img = inputs.xray12_u16(H, 300, seed=60 + r)
     np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
-    for sh in (24, 40):  # other interior strip lengths (edge strips sh/4, at least 8)
+    for sh in (24, 40):  # other interior strip lengths (edge strips of 8 rows)
         hrm.set_plan(2, 2, 300, H, 1, r, hrm.hrm_plan(128, sh, 0, 2))
         try:
             np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
