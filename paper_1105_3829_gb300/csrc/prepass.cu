@@ -3,22 +3,27 @@
 // Uniform tree (Section III, uniform IOT): the tree needs only the effective
 // bit depth d of the data (height d+1), so one max/min reduction suffices.
 //
-// Adaptive tree (Section III-C): the top-level interval boundaries follow a
-// frequency model that mixes 1:1 the source's global histogram (value
-// insertions/removals) and a histogram of a median estimate (order-statistic
-// requests).  The median estimate is the global histogram of 8x8 block means,
-// the "running mean as a first approximation" the paper suggests.  A small
-// uniform floor (1/64 of the mass) spreads boundaries over value ranges the
-// mix does not cover, so that without information the tree stays uniform
-// ("where the mix vanishes, divide equally").  The 16 top-level boundaries
-// are the equal-mass quantiles of the mix, so that every top-level child is
-// visited about equally often (the paper's optimality condition).  Any
-// boundaries give the same filter output; only the speed changes.
+// Adaptive tree (Section III-C): the top level is fitted to where the
+// order-statistic requests go, using a median estimate of the image -- here
+// the histogram of the medians of its 4x4 blocks (the paper suggests a
+// smoothed median of a typical image; block medians are robust to outliers,
+// where a running mean is not).  The central range holding 99 % of the
+// estimate gets 14 or 15 top-level intervals of one width w = 16^k, aligned
+// to w, so every sub-tree below them is a full 16-ary tree of k levels; the
+// values below and above the central range share the remaining one or two
+// (deep, rarely walked) intervals.  On this GPU design the cost of a row is
+// the number of distinct nodes its outputs visit per level, so the paper's
+// equal-visit split of the top level (which narrows top intervals around the
+// mode and leaves 1-3 bit leaf levels) is replaced by this power-of-16 split;
+// when w is not narrower than the uniform tree's top intervals the uniform
+// tree is kept.  Any boundaries give the same filter output; only the speed
+// changes.
 #include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "hist_common.cuh"
+#include "sortnet.cuh"
 
 namespace hrm {
 
@@ -66,89 +71,59 @@ __device__ __forceinline__ uint32_t prehist_binw(const LevelDesc* d) {
     return (span + PREHIST_BINS - 1) / PREHIST_BINS;
 }
 
-// Source histogram and 8x8-block-mean histogram (shared-memory privatised).
+// Histogram of 4x4 block medians (the lower median, 8th smallest of 16),
+// shared-memory privatised; partial blocks at the right and bottom edges
+// are skipped.
 template <typename T>
 __global__ void prehist_kernel(const unsigned char* __restrict__ src, size_t sp, size_t slice, int W,
                                int H, int D, const LevelDesc* d, uint32_t* hist) {
-    __shared__ uint32_t hs[PREHIST_BINS];
     __shared__ uint32_t he[PREHIST_BINS];
-    for (int i = threadIdx.x; i < PREHIST_BINS; i += blockDim.x) hs[i] = he[i] = 0;
+    for (int i = threadIdx.x; i < PREHIST_BINS; i += blockDim.x) he[i] = 0;
     __syncthreads();
     const uint32_t vmin = d->vmin;
     const uint32_t binw = prehist_binw(d);
-    const int bx = (W + 7) / 8, by = (H + 7) / 8;
+    const int bx = W / 4, by = H / 4;
     const long nblk = (long)bx * by * D;
     for (long b = (long)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += (long)gridDim.x * blockDim.x) {
         const int z = (int)(b / ((long)bx * by));
         const long rem = b % ((long)bx * by);
-        const int y0 = (int)(rem / bx) * 8, x0 = (int)(rem % bx) * 8;
-        uint32_t sum = 0, cnt = 0;
-        for (int y = y0; y < min(y0 + 8, H); ++y) {
-            const T* p = reinterpret_cast<const T*>(src + (size_t)z * slice + (size_t)y * sp);
-            for (int x = x0; x < min(x0 + 8, W); ++x) {
-                uint32_t v = __ldg(p + x);
-                sum += v;
-                ++cnt;
-                atomicAdd(&hs[(v - vmin) / binw], 1u);
-            }
+        const int y0 = (int)(rem / bx) * 4, x0 = (int)(rem % bx) * 4;
+        uint32_t v[16];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const T* p = reinterpret_cast<const T*>(src + (size_t)z * slice + (size_t)(y0 + y) * sp) + x0;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) v[4 * y + x] = __ldg(p + x);
         }
-        const uint32_t mean = (sum + cnt / 2) / cnt;
-        atomicAdd(&he[(mean - vmin) / binw], 1u);
+        sortnet<16>(v);  // values < 2^16: the packed-pair min/max act on the low half
+        atomicAdd(&he[(v[7] - vmin) / binw], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < PREHIST_BINS; i += blockDim.x) {
-        if (hs[i]) atomicAdd(&hist[i], hs[i]);
-        if (he[i]) atomicAdd(&hist[PREHIST_BINS + i], he[i]);
-    }
+    for (int i = threadIdx.x; i < PREHIST_BINS; i += blockDim.x)
+        if (he[i]) atomicAdd(&hist[i], he[i]);
 }
 
-// Equal-mass quantile boundaries of the 1:1 mix (one block of 1024 threads).
+// Top-level boundaries from the block-median histogram (one block of 1024
+// threads): the 0.5 % and 99.5 % quantiles bound the central range.
 __global__ void __launch_bounds__(1024) edges_kernel(LevelDesc* d, const uint32_t* hist) {
-    __shared__ unsigned long long cum[PREHIST_BINS + 1];
-    __shared__ unsigned long long part[1024];
-    __shared__ unsigned long long totals[2];
+    __shared__ uint32_t cum[PREHIST_BINS + 1];
+    __shared__ uint32_t part[1024];
     const int t = threadIdx.x;
-    // totals of both histograms
-    unsigned long long a = 0, b = 0;
-    for (int i = t; i < PREHIST_BINS; i += 1024) {
-        a += hist[i];
-        b += hist[PREHIST_BINS + i];
-    }
-    part[t] = a;
-    __syncthreads();
-    for (int s = 512; s > 0; s >>= 1) {
-        if (t < s) part[t] += part[t + s];
-        __syncthreads();
-    }
-    if (t == 0) totals[0] = part[0];
-    __syncthreads();
-    part[t] = b;
-    __syncthreads();
-    for (int s = 512; s > 0; s >>= 1) {
-        if (t < s) part[t] += part[t + s];
-        __syncthreads();
-    }
-    if (t == 0) totals[1] = part[0];
-    __syncthreads();
-    const unsigned long long A = totals[0] ? totals[0] : 1, B = totals[1] ? totals[1] : 1;
-    const unsigned long long floor_w = (2ull * A * B) / (64ull * PREHIST_BINS) + 1;
-    // per-thread local sums of 4 consecutive bins, then a block scan
-    unsigned long long m[4], s = 0;
+    uint32_t m[4], s = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        int i = 4 * t + k;
-        m[k] = (unsigned long long)hist[i] * B + (unsigned long long)hist[PREHIST_BINS + i] * A + floor_w;
+        m[k] = hist[4 * t + k];
         s += m[k];
     }
     part[t] = s;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
-        unsigned long long v = t >= off ? part[t - off] : 0;
+        const uint32_t v = t >= off ? part[t - off] : 0;
         __syncthreads();
         part[t] += v;
         __syncthreads();
     }
-    unsigned long long run = part[t] - s;  // exclusive prefix
+    uint32_t run = part[t] - s;  // exclusive prefix
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         cum[4 * t + k] = run;
@@ -156,29 +131,50 @@ __global__ void __launch_bounds__(1024) edges_kernel(LevelDesc* d, const uint32_
     }
     if (t == 1023) cum[PREHIST_BINS] = run;
     __syncthreads();
-    const unsigned long long total = cum[PREHIST_BINS];
+    if (t != 0) return;
+    const uint32_t total = cum[PREHIST_BINS];
     const uint32_t vmin = d->vmin, vmax = d->vmax, binw = prehist_binw(d);
-    if (t <= 16) {
-        uint32_t e;
-        if (t == 0) {
-            e = vmin;
-        } else if (t == 16) {
-            e = vmax + 1;
-        } else {
-            // smallest bin boundary i with cum[i] >= t/16 of the mass
-            unsigned long long target = (total * (unsigned long long)t) / 16;
-            int lo = 0, hi = PREHIST_BINS;
-            while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                if (cum[mid] >= target) hi = mid; else lo = mid + 1;
-            }
-            unsigned long long ev = (unsigned long long)vmin + (unsigned long long)lo * binw;
-            e = (uint32_t)min(ev, (unsigned long long)vmax + 1);
-            e = max(e, vmin);
-        }
-        d->edge[t] = e;
+    const int ushift = max(0, bitlen(vmax) - 4);
+    if (total == 0) {  // no full 4x4 block: keep the uniform tree
+        d->mode = 0;
+        return;
     }
-    if (t == 0) d->mode = 1;
+    // bin a holds the 0.5 % quantile (cum[a] <= lo_t < cum[a+1]), bin b the
+    // 99.5 % one (cum[b] < hi_t <= cum[b+1]); cum is non-decreasing
+    const uint64_t lo_t = (uint64_t)total * 5 / 1000, hi_t = (uint64_t)total * 995 / 1000;
+    int lo = 0, hi = PREHIST_BINS - 1;
+    while (lo < hi) {  // first i with cum[i+1] > lo_t
+        const int mid = (lo + hi) >> 1;
+        if (cum[mid + 1] > lo_t) hi = mid; else lo = mid + 1;
+    }
+    const int a = lo;
+    lo = a;
+    hi = PREHIST_BINS - 1;
+    while (lo < hi) {  // last i with cum[i] < hi_t
+        const int mid = (lo + hi + 1) >> 1;
+        if (cum[mid] < hi_t) lo = mid; else hi = mid - 1;
+    }
+    const int b = lo;
+    const uint64_t av = (uint64_t)vmin + (uint64_t)a * binw;
+    uint64_t bv = (uint64_t)vmin + (uint64_t)(b + 1) * binw - 1;
+    if (bv > vmax) bv = vmax;
+    // smallest w = 16^k with 13 w >= the central range (one interval of slack for the alignment)
+    uint64_t w = 16;
+    while (13 * w < bv - av + 1) w <<= 4;
+    if (ushift <= 0 || w >= (1ull << ushift)) {  // not finer than the uniform tree
+        d->mode = 0;
+        return;
+    }
+    const uint64_t base = (av / w) * w;
+    const uint64_t top = (uint64_t)vmax + 1;
+    uint64_t e[17];
+    e[0] = vmin;
+    int c = 1;
+    if (base > vmin) e[c++] = base;
+    for (uint64_t i = 1; c < 16; ++i) e[c++] = base + i * w < top ? base + i * w : top;
+    e[16] = top;
+    for (int k = 0; k <= 16; ++k) d->edge[k] = (uint32_t)(e[k] < top ? e[k] : top);
+    d->mode = 1;
 }
 
 cudaError_t launch_levels(int elem, bool adaptive, const void* src, size_t sp, size_t slice, int W,
