@@ -32,7 +32,7 @@ static_assert(sizeof(LevelDesc) == 128, "LevelDesc layout");
 enum CountId {
     CNT_TILES = 0, CNT_ROWS, CNT_CYC_TOTAL, CNT_CYC_INIT, CNT_CYC_COLUMNS, CNT_CYC_RESOLVE,
     CNT_CYC_INSTALL, CNT_CYC_WINDOW, CNT_CYC_ADVANCE, CNT_INSTALLS, CNT_ROUNDS, CNT_PREFIXES,
-    CNT_DIRECT_ROUNDS, CNT_LEVELS, CNT_NUM
+    CNT_DIRECT_ROUNDS, CNT_LEVELS, CNT_CYC_ALLOC, CNT_NUM
 };
 #ifdef HRM_COUNT_OPS
 static __device__ unsigned long long g_hrm_counters[CNT_NUM];
@@ -87,7 +87,7 @@ struct OpCounters {
 constexpr uint32_t KEY_NONE = 0xFFFFFFFFu;
 constexpr int HASH_SIZE = 64;
 constexpr int MAX_SLOTS = 32;
-constexpr int META_BYTES = 3072;  // per-tile metadata block (see Meta)
+constexpr int META_BYTES = 4096;  // per-tile metadata block (see Meta)
 // Node requests recorded per round.  A round installs at most one node per
 // free slot (< MAX_SLOTS), so later requests would wait for the next round
 // anyway; requests that find the tables full are simply retried then.
@@ -120,6 +120,15 @@ struct Meta {
     uint32_t build_slot[MAX_SLOTS];
     uint32_t build_key[MAX_SLOTS];
     uint32_t wtot[8][8];        // per-warp totals of the block prefix scan
+    // Column spans.  A node below the root is built only over the tile
+    // columns its requesting outputs' windows cover (plus a margin) and
+    // widened in place when a later output needs more; clo/chi is the range
+    // of a slot's records that hold counts (the rest is stale).
+    int16_t clo[MAX_SLOTS], chi[MAX_SLOTS];
+    int32_t preq_lo[PREQ_SIZE], preq_hi[PREQ_SIZE];  // span wanted by each pending request
+    uint8_t req_h[REQ_MAX];                           // its pending-hash position
+    int16_t build_lo[MAX_SLOTS], build_hi[MAX_SLOTS];  // columns of each build entry
+    uint32_t build_off[MAX_SLOTS + 1];                // prefix of the entries' widths
     // Per-round bookkeeping, triple-buffered: round k uses rs[k % 3] and
     // clears rs[(k + 1) % 3] for round k + 1.  The first round of a level is
     // resolved before the barrier that closes the previous level, while other
@@ -189,7 +198,13 @@ __device__ __forceinline__ void slots_reset(Meta& m) {
     reinterpret_cast<uint32_t*>(m.lut2)[lane] = 0xFFFFFFFFu;
     reinterpret_cast<uint32_t*>(m.lut2)[lane + 32] = 0xFFFFFFFFu;
 #pragma unroll
-    for (int i = lane; i < PREQ_SIZE; i += 32) m.preq[i] = KEY_NONE;
+    for (int i = lane; i < PREQ_SIZE; i += 32) {
+        m.preq[i] = KEY_NONE;
+        m.preq_lo[i] = 0x7FFFFFFF;
+        m.preq_hi[i] = -1;
+    }
+    m.clo[lane] = 0x7FFF;
+    m.chi[lane] = -1;
     for (int b = 0; b < 3; ++b) {
         m.rs[b].span_lo[lane] = 0x7FFFFFFF;
         m.rs[b].span_hi[lane] = -1;
@@ -221,36 +236,51 @@ __device__ __forceinline__ void round_clear(Meta::Round& rb) {
 // Record a missing node for this round; duplicates collapse through a small
 // hash of pending keys.  A request that finds the table full is simply not
 // recorded (its outputs retry next round; the first request always fits).
-__device__ __forceinline__ void request_node(Meta& m, Meta::Round& rb, uint32_t key) {
+__device__ __forceinline__ void request_node(Meta& m, Meta::Round& rb, uint32_t key, int lo, int hi) {
     uint32_t h = hash_of(key) & (PREQ_SIZE - 1);
     for (int i = 0; i < PREQ_SIZE; ++i) {
         const uint32_t prev = atomicCAS(&m.preq[h], KEY_NONE, key);
-        if (prev == KEY_NONE) {
-            const uint32_t at = atomicAdd(&rb.nreq, 1u);
-            if (at < REQ_MAX) m.req[at] = key;
+        if (prev == KEY_NONE || prev == key) {
+            atomicMin(&m.preq_lo[h], lo);
+            atomicMax(&m.preq_hi[h], hi);
+            if (prev == KEY_NONE) {
+                const uint32_t at = atomicAdd(&rb.nreq, 1u);
+                if (at < REQ_MAX) {
+                    m.req[at] = key;
+                    m.req_h[at] = (uint8_t)h;
+                }
+            }
             return;
         }
-        if (prev == key) return;
         h = (h + 1) & (PREQ_SIZE - 1);
     }
 }
 
-// Give slot v to node nk (whole warp): update the direct tables in O(1), the
-// hash only when a level >= 3 node enters or leaves, and the level masks.
-__device__ __forceinline__ void slot_assign(Meta& m, int nslots, int v, uint32_t nk) {
-    const int lane = threadIdx.x & 31;
+// Do the records of slot s hold counts for the window columns [xl, xl+2r]?
+__device__ __forceinline__ bool span_ok(const Meta& m, int s, int xl, int r) {
+    return (int)m.clo[s] <= xl && xl + 2 * r <= (int)m.chi[s];
+}
+
+// Give slot v to node nk (one thread): the direct tables of levels 1 and 2
+// are updated in O(1); returns whether a level >= 3 node left or entered
+// (the hash of deep nodes then needs slot_tables_refresh).
+__device__ __forceinline__ bool slot_set_key(Meta& m, int v, uint32_t nk) {
     const uint32_t ok = m.key[v];
-    const int ol = ok == KEY_NONE ? 0 : (int)(ok >> 20), nl = (int)(nk >> 20);
+    const int ol = ok == KEY_NONE ? 0 : (int)(ok >> 20), nl = nk == KEY_NONE ? 0 : (int)(nk >> 20);
+    if (ol == 1) m.lut1[(ok >> 16) & 15] = NO_SLOT;
+    if (ol == 2) m.lut2[(((ok >> 16) & 15) << 4) | (ok & 15)] = NO_SLOT;
+    if (nl == 1) m.lut1[(nk >> 16) & 15] = (uint8_t)v;
+    if (nl == 2) m.lut2[(((nk >> 16) & 15) << 4) | (nk & 15)] = (uint8_t)v;
+    m.key[v] = nk;
+    return ol >= 3 || nl >= 3;
+}
+
+// After a round's slot assignments (whole warp): level masks from all slot
+// keys and, when deep nodes changed, the hash of deep nodes (lanes insert
+// their own slot's key concurrently with linear probing).
+__device__ __forceinline__ void slot_tables_refresh(Meta& m, int nslots, bool deep_changed) {
+    const int lane = threadIdx.x & 31;
     __syncwarp();
-    if (lane == 0) {
-        if (ol == 1) m.lut1[(ok >> 16) & 15] = NO_SLOT;
-        if (ol == 2) m.lut2[(((ok >> 16) & 15) << 4) | (ok & 15)] = NO_SLOT;
-        if (nl == 1) m.lut1[(nk >> 16) & 15] = (uint8_t)v;
-        if (nl == 2) m.lut2[(((nk >> 16) & 15) << 4) | (nk & 15)] = (uint8_t)v;
-        m.key[v] = nk;
-    }
-    __syncwarp();
-    // level masks from all slot keys
     const uint32_t k = (lane > 0 && lane < nslots) ? m.key[lane] : KEY_NONE;
     const int kl = k == KEY_NONE ? 0 : (int)(k >> 20);
     const uint32_t bit = k == KEY_NONE ? 0u : 1u << ((k >> 16) & 15);
@@ -266,18 +296,17 @@ __device__ __forceinline__ void slot_assign(Meta& m, int nslots, int v, uint32_t
         m.lmask[0] = any;
         m.ndeep = deep;
     }
-    if (ol >= 3 || nl >= 3) {  // rebuild the hash of deep nodes
+    if (deep_changed) {
         m.hash[lane] = KEY_NONE;
         m.hash[lane + 32] = KEY_NONE;
         __syncwarp();
-        if (lane == 0)
-            for (int s = 1; s < nslots; ++s) {
-                const uint32_t kk = m.key[s];
-                if (kk == KEY_NONE || (kk >> 20) < 3) continue;
-                uint32_t h = hash_of(kk);
-                while (m.hash[h] != KEY_NONE) h = (h + 1) & (HASH_SIZE - 1);
-                m.hash[h] = (kk << 8) | (uint32_t)s;
+        if (kl >= 3) {
+            uint32_t h = hash_of(k);
+            for (int i = 0; i < HASH_SIZE; ++i) {  // <= 31 keys in 64 entries: always finds room
+                if (atomicCAS(&m.hash[h], KEY_NONE, (k << 8) | (uint32_t)lane) == KEY_NONE) break;
+                h = (h + 1) & (HASH_SIZE - 1);
             }
+        }
     }
     __syncwarp();
 }

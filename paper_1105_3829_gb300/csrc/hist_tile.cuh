@@ -45,6 +45,9 @@ namespace hrm {
 
 constexpr int BLOCK_WARPS = 4;     // warps per tile
 constexpr int BLOCK_THREADS = 32 * BLOCK_WARPS;
+// Extra columns on each side of a requested node span, so that medians
+// drifting sideways by a few columns per row do not widen it every row.
+constexpr int SPAN_MARGIN = 16;
 
 struct HistJob {
     const unsigned char* src;
@@ -182,8 +185,9 @@ __device__ __forceinline__ int node_digit(const Meta& m, const NodeRange& nr, ui
     return (int)((v - nr.lo) >> nr.dshift);
 }
 
-// Build the records of m.nbuild new slots at walk position t (whole block):
-// work items (slot, column) are spread over the threads; values come from the
+// Build the records of the m.nbuild build entries (slot, column range) at walk
+// position t (whole block): work items (entry, column) are spread over the
+// threads in column order; values come from the
 // shared-memory ring when present (2D), else from global memory with eight
 // loads in flight per thread.  The index arithmetic per value is kept to a
 // clamp and a multiply-add (no division): installs near the image corners,
@@ -194,9 +198,11 @@ __device__ void build_slots(const HistJob& a, const Geo& g, const Meta& m, unsig
     const int r = a.r;
     const int n = 2 * r + 1;
     const int nb = (int)m.nbuild;
-    const int items = nb * NC;
+    const int items = (int)m.build_off[nb];
+    int b = 0;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int b = it / NC, cx = it - b * NC;
+        while (b + 1 < nb && (int)m.build_off[b + 1] <= it) ++b;  // items ascend per thread
+        const int cx = (int)m.build_lo[b] + (it - (int)m.build_off[b]);
         const NodeRange nr = node_range(m, m.build_key[b]);
         uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (ring) {
@@ -486,6 +492,12 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         m.nbuild = 1;
         m.build_slot[0] = 0;
         m.build_key[0] = 0;
+        m.build_lo[0] = 0;
+        m.build_hi[0] = (int16_t)(NC - 1);
+        m.build_off[0] = 0;
+        m.build_off[1] = NC;
+        m.clo[0] = 0;
+        m.chi[0] = (int16_t)(NC - 1);
     }
     __syncthreads();
     build_slots<T, CW>(a, g, m, slots, NC, x0, ts, ring);
@@ -643,14 +655,17 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                 slot[k] = -1;
                 hit[k] = false;
                 if (todo[k]) {
-                    const int s = slot_lookup(m, level, cbin[k], pre[k]);
+                    const int xl = tid + NT * k;
+                    int s = slot_lookup(m, level, cbin[k], pre[k]);
+                    if (s >= 0 && !span_ok(m, s, xl, r)) s = -1;  // resident, but not over this window
                     slot[k] = s;
                     if (s >= 0) {
                         m.pin[s] = pass_id;
                         hit[k] = true;
                         ++nres;
                     } else {
-                        request_node(m, rb, node_key(level, cbin[k], pre[k]));
+                        request_node(m, rb, node_key(level, cbin[k], pre[k]), max(xl - SPAN_MARGIN, 0),
+                                     min(xl + 2 * r + SPAN_MARGIN, NC - 1));
                     }
                 }
             }
@@ -692,29 +707,74 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                     // warp 0 gives unpinned slots (least recently used first)
                     // to the requested nodes; the block builds them
                     if (warp == 0) {
+                        // A request for a resident node (its span was too
+                        // narrow) widens that slot in place: only the new
+                        // columns are built.  Otherwise the least recently
+                        // used unpinned slot is taken and built over the span.
                         const uint32_t nr = min(nreq, (uint32_t)REQ_MAX);
-                        uint32_t nb = 0;
-                        for (uint32_t i = 0; i < nr; ++i) {
-                            uint32_t cand = 0xFFFFFFFFu;
-                            if (lane > 0 && lane < S && m.pin[lane] != pass_id)
-                                cand = (m.stamp[lane] << 5) | (uint32_t)lane;
-                            cand = __reduce_min_sync(0xffffffffu, cand);
-                            if (cand == 0xFFFFFFFFu) break;  // every slot is in use this round
-                            const int victim = (int)(cand & 31u);
-                            slot_assign(m, S, victim, m.req[i]);
-                            if (lane == 0) {
-                                m.pin[victim] = pass_id;
-                                m.stamp[victim] = stampv;
-                                m.build_slot[nb] = (uint32_t)victim;
-                                m.build_key[nb] = m.req[i];
+                        uint32_t nb = 0, off = 0;
+                        bool deep_changed = false;
+                        for (uint32_t i = 0; i < nr && nb + 2 <= (uint32_t)MAX_SLOTS; ++i) {
+                            const uint32_t key = m.req[i];
+                            const int h = m.req_h[i];
+                            int lo = m.preq_lo[h], hi = m.preq_hi[h];
+                            int slot_w = slot_lookup(m, key);
+                            // (the deep-node hash is refreshed after the loop: a slot
+                            // reassigned earlier in this loop may still be listed)
+                            if (slot_w >= 0 && m.key[slot_w] != key) slot_w = -1;
+                            int part_lo[2] = {lo, 0}, part_hi[2] = {hi, -1};
+                            if (slot_w >= 0) {
+                                const int olo = m.clo[slot_w], ohi = m.chi[slot_w];
+                                // the union must stay contiguous: build from the new
+                                // edge up to the old span on each side (gaps included)
+                                part_lo[0] = lo;
+                                part_hi[0] = olo - 1;
+                                part_lo[1] = ohi + 1;
+                                part_hi[1] = hi;
+                                lo = min(lo, olo);
+                                hi = max(hi, ohi);
+                            } else {
+                                uint32_t cand = 0xFFFFFFFFu;
+                                if (lane > 0 && lane < S && m.pin[lane] != pass_id)
+                                    cand = (m.stamp[lane] << 5) | (uint32_t)lane;
+                                cand = __reduce_min_sync(0xffffffffu, cand);
+                                if (cand == 0xFFFFFFFFu) break;  // every slot is in use this round
+                                slot_w = (int)(cand & 31u);
+                                if (lane == 0) deep_changed |= slot_set_key(m, slot_w, key);
                             }
-                            ++nb;
+                            if (lane == 0) {
+                                m.pin[slot_w] = pass_id;
+                                m.stamp[slot_w] = stampv;
+                                m.clo[slot_w] = (int16_t)lo;
+                                m.chi[slot_w] = (int16_t)hi;
+                                for (int q = 0; q < 2; ++q) {
+                                    if (part_hi[q] < part_lo[q]) continue;
+                                    m.build_slot[nb] = (uint32_t)slot_w;
+                                    m.build_key[nb] = key;
+                                    m.build_lo[nb] = (int16_t)part_lo[q];
+                                    m.build_hi[nb] = (int16_t)part_hi[q];
+                                    m.build_off[nb] = off;
+                                    off += (uint32_t)(part_hi[q] - part_lo[q] + 1);
+                                    ++nb;
+                                }
+                            }
+                            nb = __shfl_sync(0xffffffffu, nb, 0);
+                            off = __shfl_sync(0xffffffffu, off, 0);
                             __syncwarp();
                         }
-                        for (int i = lane; i < PREQ_SIZE; i += 32) m.preq[i] = KEY_NONE;
-                        if (lane == 0) m.nbuild = nb;
+                        slot_tables_refresh(m, S, __shfl_sync(0xffffffffu, (int)deep_changed, 0) != 0);
+                        for (int i = lane; i < PREQ_SIZE; i += 32) {
+                            m.preq[i] = KEY_NONE;
+                            m.preq_lo[i] = 0x7FFFFFFF;
+                            m.preq_hi[i] = -1;
+                        }
+                        if (lane == 0) {
+                            m.nbuild = nb;
+                            m.build_off[nb] = off;
+                        }
                     }
                     __syncthreads();
+                    oc.lap(CNT_CYC_ALLOC);
                     build_slots<T, CW>(a, g, m, slots, NC, x0, t, ring);
                     oc.add(CNT_INSTALLS, m.nbuild);
                     bool got[PPL];
@@ -723,7 +783,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                         got[k] = false;
                         if (todo[k] && slot[k] < 0) {
                             const int s2 = slot_lookup(m, level, cbin[k], pre[k]);
-                            if (s2 >= 0 && m.pin[s2] == pass_id) {
+                            if (s2 >= 0 && m.pin[s2] == pass_id && span_ok(m, s2, tid + NT * k, r)) {
                                 slot[k] = s2;
                                 got[k] = true;
                                 ++nres;
