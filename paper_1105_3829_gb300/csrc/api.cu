@@ -309,7 +309,14 @@ int filter_impl(const Image& im, int r, long rank, unsigned flags, int drop_bits
     const PlanH p = resolve_plan(im.dtype, im.dims, im.W, im.H, im.D, r, flags, di, force);
     cudaError_t e;
     if (im.dims == 2 && p.path == 1 && r <= SORTNET_MAX_R2D && median && drop_bits == 0) {
-        e = launch_sortnet2d(es, r, im.src, im.sp, im.dst, im.dp, im.W, im.H, 32, st);
+        // rows per warp: about 32 warp tiles per SM (latency hiding for the
+        // memory-bound 3x3 network), but at least 8 rows so the 2r rows each
+        // warp reads ahead stay a small share
+        const long tw = r <= 2 ? 256 : 2 * (32 - 2 * ((r + 1) / 2));
+        const long tiles_x = (im.W + tw - 1) / tw;
+        const long want = (long)di.num_sms * 32;
+        const int rpw = (int)std::max(8L, std::min(32L, (im.H * tiles_x + want - 1) / want));
+        e = launch_sortnet2d(es, r, im.src, im.sp, im.dst, im.dp, im.W, im.H, rpw, st);
         return e == cudaSuccess ? HRM_OK : cuda_fail(e, "sortnet launch");
     }
     if (im.dims == 3 && p.path == 1 && r == 1 && median && drop_bits == 0 && im.H <= 65535) {

@@ -13,9 +13,10 @@ namespace hrm {
 // Top level: 16 coarse intervals [e_c, e_{c+1}).  Uniform mode (Section III,
 // uniform IOT): e_c = c << shift with shift = max(0, bitlen(vmax) - 4), i.e.
 // the tree of effective bit depth d = bitlen(vmax) anchored at 0.  Adaptive
-// mode (Section III-C): e_c are data-driven (equal-mass quantiles of the mixed
-// frequency model).  Below each coarse interval the tree is uniform, with
-// D_c = bitlen(width_c - 1) bits taken 4 bits (16 children) per level.
+// mode (Section III-C): e_c are data-driven (a power-of-16 split of the range
+// a median estimate occupies; see prepass.cu).  Below each coarse interval the
+// tree is uniform, with D_c = bitlen(width_c - 1) bits taken 4 bits (16
+// children) per level.
 struct LevelDesc {
     uint32_t mode;      // 0 = uniform, 1 = adaptive
     uint32_t vmin;      // observed minimum (filled by the pre-pass)
