@@ -315,9 +315,75 @@ def run_secondary(args):
                                                                "512^2 uint8 uniform r=3"),
               "Mpix/s", value, {"dtype": dt, "cases": res,
                                 "config": {"workload": args.workload, "l2": "flushed before every timed call"}}, args)
+    elif args.workload == "video":
+        run_video(args, hrm, inputs, torch, dev, flush)
+    elif args.workload == "paper":
+        run_paper(args, hrm, inputs, torch, dev, flush)
     else:
         run_serve(args, hrm, inputs, torch, dev)
     return 0
+
+
+def run_video(args, hrm, inputs, torch, dev, flush):
+    """Frame stream (8 frames of 4096^2 uint16 low-key content with blobs
+    drifting 4 px per frame): per-frame time of the uniform tree, the
+    image-based adaptive tree, and the topology carried from the previous
+    frame's medians (Section III-C).  Outputs are identical in all three."""
+    frames = [torch.from_numpy(f).to(dev) for f in inputs.video_frames(8, 4096, 4096, drift=4)]
+    out = torch.empty_like(frames[0])
+    res = {}
+    for r in (15, 50):
+        row = {}
+        for mode in ("uniform", "adaptive", "video"):
+            topo = hrm.Topology() if mode == "video" else None
+            times = []
+            for rep in range(2):  # the first pass warms up the plan (and the topology)
+                for f in frames:
+                    flush.fill_(1)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    if mode == "video":
+                        hrm.filter2d_video(f, r, topo, out=out)
+                    else:
+                        hrm.filter2d(f, r, adaptive=(mode == "adaptive"), out=out)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    if rep:
+                        times.append(e0.elapsed_time(e1))
+            if topo:
+                topo.close()
+            row[mode] = {"ms_per_frame": float(np.mean(times)), "mpix_s": out.numel() / float(np.mean(times)) / 1e3}
+        res["r%d" % r] = row
+    value = float(np.mean([res[k]["video"]["mpix_s"] for k in res]))
+    _line("frame stream: output Mpix/s with the previous frame's topology (mean over r=15,50)", "Mpix/s", value,
+          {"dtype": "u16", "cases": res, "config": {"workload": "video: 8 frames 4096^2 uint16 low-key, blobs "
+                                                    "drifting 4 px/frame", "l2": "flushed before every timed call"}},
+          args)
+
+
+def run_paper(args, hrm, inputs, torch, dev, flush):
+    """The paper's synthetic workloads at its window n = 51 (r = 25),
+    4096^2: random normal (mid-range mean, 3 sigma = half range) and diagonal
+    sines of period 100 / 25 px, 8-bit and 16-bit, uniform and adaptive tree.
+    The paper's single-core CPU figures (Tables I/II) are context only."""
+    cases = {"normal8": inputs.paper_normal(4096, 4096, 8, seed=inputs.seed_for(7, 1)),
+             "sine100_8": inputs.paper_sine(4096, 4096, 100, 8),
+             "sine25_8": inputs.paper_sine(4096, 4096, 25, 8),
+             "normal16": inputs.paper_normal(4096, 4096, 16, seed=inputs.seed_for(7, 2)),
+             "sine100_16": inputs.paper_sine(4096, 4096, 100, 16)}
+    res = {}
+    for name, a in cases.items():
+        img = torch.from_numpy(a).to(dev)
+        out = torch.empty_like(img)
+        for ad in (False, True):
+            t = _timed(lambda: hrm.filter2d(img, 25, adaptive=ad, out=out), flush, max(3, args.steps))
+            ms = float(np.median(t))
+            res["%s%s" % (name, "_adaptive" if ad else "")] = {"p50_ms": ms, "mpix_s": img.numel() / ms / 1e3}
+    value = float(np.mean([v["mpix_s"] for v in res.values()]))
+    _line("paper synthetic workloads at r=25 (4096^2): output Mpix/s (mean over cases)", "Mpix/s", value,
+          {"dtype": "u8+u16", "cases": res, "config": {"workload": "paper: random normal and diagonal sines, "
+                                                       "8/16-bit, r=25", "l2": "flushed before every timed call"}},
+          args)
 
 
 def run_serve(args, hrm, inputs, torch, dev):
@@ -395,7 +461,7 @@ def main():
                     help="--impl reference: seconds of oracle work per step (default: 90 s over all steps, 2..20 s)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--workload", default="xray2d",
-                    choices=["xray2d", "volume3d", "lowkey2d", "u8small", "serve"],
+                    choices=["xray2d", "volume3d", "lowkey2d", "u8small", "serve", "video", "paper"],
                     help="xray2d (default) is the benchmark workload; the others are the secondary configs")
     ap.add_argument("--rates", default="100,300,1000,3000,5000", help="serve: Poisson arrival rates (1/s)")
     ap.add_argument("--requests", type=int, default=10000, help="serve: requests per rate (capped at rate x 10 s)")

@@ -122,6 +122,29 @@ int hrm_filter2d_lowprec(int dtype, const void* src, size_t src_pitch, void* dst
                          size_t dst_pitch, int width, int height, int radius, int drop_bits,
                          void* stream);
 
+/* ---- frame streams: the previous frame's medians as the median estimate ----
+ *
+ * Section III-C names the previous frame's median as one source of the
+ * median estimate that shapes the adaptive tree.  A topology object carries
+ * that estimate from one frame to the next: hrm_filter2d_video filters a
+ * frame with the top level derived from the previous frame's output (the
+ * first frame, or a frame of another dtype, uses the image's own adaptive
+ * pre-pass), then histograms its own output for the next frame.  Outputs are
+ * always the exact median (identical to hrm_filter2d); only the speed
+ * depends on how well consecutive frames agree.
+ *
+ * The topology holds device state (about 17 KB, allocated by create on the
+ * current device) that each call reads and rewrites asynchronously on its
+ * stream: calls that share a topology must be ordered (one stream, or events),
+ * and the topology must outlive them.  create: HRM_ENOMEM if the allocation
+ * fails.  video: HRM_EINVAL for a null topology or one created on another
+ * device, plus hrm_filter2d's argument errors. */
+typedef struct hrm_topology hrm_topology;
+int hrm_topology_create(hrm_topology** out);
+int hrm_topology_destroy(hrm_topology* topo);
+int hrm_filter2d_video(int dtype, const void* src, size_t src_pitch, void* dst, size_t dst_pitch,
+                       int width, int height, int radius, hrm_topology* topo, void* stream);
+
 /* ---- batched form: many images of uneven size and radius, one launch ----
  *
  * hrm_filter_batch runs every job in ONE persistent kernel launch (plus the

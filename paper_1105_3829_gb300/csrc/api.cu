@@ -2,6 +2,8 @@
 // device info, error reporting and planning.
 #include <cuda_runtime.h>
 
+#include <new>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -297,7 +299,7 @@ static int copy_image(const Image& im, cudaStream_t st) {
 }
 
 int filter_impl(const Image& im, int r, long rank, unsigned flags, int drop_bits, const hrm_plan* force,
-                cudaStream_t st) {
+                cudaStream_t st, const LevelDesc* given) {
     if (im.W == 0 || im.H == 0 || im.D == 0) return HRM_OK;
     const int es = im.dtype == HRM_U16 ? 2 : 1;
     const long n = 2L * r + 1, N = im.dims == 3 ? n * n * n : n * n;
@@ -327,8 +329,8 @@ int filter_impl(const Image& im, int r, long rank, unsigned flags, int drop_bits
     int rc = workspace_for(st, &ws);
     if (rc) return rc;
     const bool adaptive = (flags & HRM_ADAPTIVE) != 0;
-    const LevelDesc* desc = nullptr;
-    if (es == 2 || adaptive) {
+    const LevelDesc* desc = given;
+    if (!desc && (es == 2 || adaptive)) {
         e = launch_levels(es, adaptive, im.src, im.sp, im.dims == 3 ? im.sslice : 0, im.W, im.H,
                           im.dims == 3 ? im.D : 1, ws->desc, ws->hist, di.num_sms, st);
         if (e != cudaSuccess) return cuda_fail(e, "level pre-pass launch");
@@ -401,6 +403,61 @@ int hrm_filter2d_lowprec(int dtype, const void* src, size_t src_pitch, void* dst
     if (drop_bits == 0) return filter_impl(im, radius, -1, 0, 0, nullptr, (cudaStream_t)stream);
     hrm_plan force{0, 0, 0, 2};  // the early-stopping walk lives in the histogram kernel
     return filter_impl(im, radius, -1, 0, drop_bits, &force, (cudaStream_t)stream);
+}
+
+struct hrm_topology {
+    int device = -1;
+    int dtype = 0;      // dtype of the frame the descriptor was made from (0: none yet)
+    LevelDesc* desc = nullptr;
+    uint32_t* hist = nullptr;
+};
+
+int hrm_topology_create(hrm_topology** out) {
+    if (!out) return fail(HRM_EINVAL, "null topology pointer");
+    *out = nullptr;
+    auto* t = new (std::nothrow) hrm_topology();
+    if (!t) return fail(HRM_ENOMEM, "topology");
+    cudaGetDevice(&t->device);
+    if (cudaMalloc(&t->desc, sizeof(LevelDesc)) != cudaSuccess ||
+        cudaMalloc(&t->hist, sizeof(uint32_t) * 4096) != cudaSuccess) {
+        cudaFree(t->desc);
+        cudaFree(t->hist);
+        delete t;
+        clear_error();
+        return fail(HRM_ENOMEM, "topology device buffers");
+    }
+    *out = t;
+    return HRM_OK;
+}
+
+int hrm_topology_destroy(hrm_topology* t) {
+    if (!t) return HRM_OK;
+    cudaDeviceSynchronize();  // calls that use the topology may still be in flight
+    cudaFree(t->desc);
+    cudaFree(t->hist);
+    delete t;
+    return HRM_OK;
+}
+
+int hrm_filter2d_video(int dtype, const void* src, size_t src_pitch, void* dst, size_t dst_pitch, int width,
+                       int height, int radius, hrm_topology* topo, void* stream) {
+    if (!topo) return fail(HRM_EINVAL, "null topology");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != topo->device) return fail(HRM_EINVAL, "topology belongs to another device");
+    Image im{dtype, 2, src, dst, src_pitch, 0, dst_pitch, 0, width, height, 1};
+    int rc = validate(im, radius, HRM_BORDER_REPLICATE, 0);
+    if (rc) return rc;
+    if (width == 0 || height == 0) return HRM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const LevelDesc* given = topo->dtype == dtype ? topo->desc : nullptr;
+    rc = filter_impl(im, radius, -1, given ? 0u : (unsigned)HRM_ADAPTIVE, 0, nullptr, st, given);
+    if (rc) return rc;
+    const cudaError_t e = launch_topology_from_output(dtype == HRM_U16 ? 2 : 1, dst, dst_pitch, width, height,
+                                                      topo->desc, topo->hist, device_info().num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(e, "topology update launch");
+    topo->dtype = dtype;
+    return HRM_OK;
 }
 
 int hrm_device_status(void* stream) {

@@ -220,3 +220,49 @@ cudaError_t launch_levels_adaptive_only(int elem, const void* src, size_t sp, si
 }
 
 }  // namespace hrm
+
+namespace hrm {
+
+// Histogram of a filtered frame's values over the whole dtype range (the
+// descriptor's vmin/vmax are set to 0 and 2^bits - 1 first).
+template <typename T>
+__global__ void outhist_kernel(const unsigned char* __restrict__ img, size_t pitch, int W, int H,
+                               const LevelDesc* d, uint32_t* hist) {
+    __shared__ uint32_t hs[PREHIST_BINS];
+    for (int i = threadIdx.x; i < PREHIST_BINS; i += blockDim.x) hs[i] = 0;
+    __syncthreads();
+    const uint32_t binw = prehist_binw(d);
+    const int lane = threadIdx.x & 31;
+    const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
+    for (long y = warp; y < H; y += nwarps) {
+        const T* p = reinterpret_cast<const T*>(img + (size_t)y * pitch);
+        for (int x = lane; x < W; x += 32) atomicAdd(&hs[(uint32_t)__ldg(p + x) / binw], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < PREHIST_BINS; i += blockDim.x)
+        if (hs[i]) atomicAdd(&hist[i], hs[i]);
+}
+
+__global__ void full_range_kernel(LevelDesc* d, int elem) {
+    if (threadIdx.x == 0) {
+        d->vmin = 0;
+        d->vmax = elem == 2 ? 65535u : 255u;
+    }
+}
+
+cudaError_t launch_topology_from_output(int elem, const void* dst, size_t dp, int W, int H, LevelDesc* desc,
+                                        uint32_t* hist, int num_sms, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * PREHIST_BINS, st);
+    if (e != cudaSuccess) return e;
+    full_range_kernel<<<1, 32, 0, st>>>(desc, elem);
+    int blocks = (int)std::min<long>(((long)H + 7) / 8, (long)num_sms * 2);
+    if (blocks < 1) blocks = 1;
+    auto s = (const unsigned char*)dst;
+    if (elem == 1) outhist_kernel<uint8_t><<<blocks, 256, 0, st>>>(s, dp, W, H, desc, hist);
+    else outhist_kernel<uint16_t><<<blocks, 256, 0, st>>>(s, dp, W, H, desc, hist);
+    edges_kernel<<<1, 1024, 0, st>>>(desc, hist);
+    return cudaGetLastError();
+}
+
+}  // namespace hrm

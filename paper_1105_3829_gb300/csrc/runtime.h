@@ -71,6 +71,10 @@ cudaError_t launch_sortnet2d(int elem, int radius, const void* src, size_t sp, v
 cudaError_t launch_sortnet3d(int elem, const void* src, size_t sp, size_t ss, void* dst, size_t dp, size_t ds,
                              int W, int H, int D, int zn, cudaStream_t st);
 cudaError_t launch_hist(const HistJob& job, cudaStream_t st);
+// Video topology: histogram of a filtered frame (the median estimate for the
+// next frame) and the top-level boundaries from it.
+cudaError_t launch_topology_from_output(int elem, const void* dst, size_t dp, int W, int H, LevelDesc* desc,
+                                        uint32_t* hist, int num_sms, cudaStream_t st);
 cudaError_t launch_levels(int elem, bool adaptive, const void* src, size_t sp, size_t slice, int W,
                           int H, int D, LevelDesc* desc, uint32_t* hist, int num_sms,
                           cudaStream_t st);
@@ -84,7 +88,7 @@ struct Image {
     int W, H, D;
 };
 int filter_impl(const Image& im, int r, long rank, unsigned flags, int drop_bits, const hrm_plan* force,
-                cudaStream_t st);
+                cudaStream_t st, const LevelDesc* given = nullptr);
 int validate(const Image& im, int r, int border, unsigned flags);
 // Fill a HistJob (pre-pass descriptor supplied by the caller) for one image.
 int make_hist_job(const Image& im, int r, uint32_t K, unsigned flags, int drop_bits, const PlanH& p,

@@ -74,6 +74,9 @@ SIGNATURES = {
     "hrm_rank_filter2d": (_I, [_I, _P, _S, _P, _S, _I, _I, _I, _L, _I, _U, _P]),
     "hrm_rank_filter3d": (_I, [_I, _P, _S, _S, _P, _S, _S, _I, _I, _I, _I, _L, _I, _U, _P]),
     "hrm_filter2d_lowprec": (_I, [_I, _P, _S, _P, _S, _I, _I, _I, _I, _P]),
+    "hrm_topology_create": (_I, [C.POINTER(_P)]),
+    "hrm_topology_destroy": (_I, [_P]),
+    "hrm_filter2d_video": (_I, [_I, _P, _S, _P, _S, _I, _I, _I, _P, _P]),
     "hrm_filter_batch": (_I, [C.POINTER(hrm_job), _I, _P]),
     "hrm_filter_batch_noalloc": (_I, [C.POINTER(hrm_job), _I, _P]),
     "hrm_batch_graph_create": (_I, [C.POINTER(hrm_job), _I, _P, C.POINTER(_P)]),
@@ -306,6 +309,39 @@ def set_plan(dtype: int, dims: int, width: int, height: int, depth: int, radius:
              adaptive: bool = False) -> None:
     check(lib().hrm_set_plan(dtype, dims, width, height, depth, radius, HRM_ADAPTIVE if adaptive else 0,
                              C.byref(plan)), "hrm_set_plan")
+
+
+class Topology:
+    """Frame-to-frame median estimate for hrm_filter2d_video (device state)."""
+
+    def __init__(self):
+        h = _P()
+        check(lib().hrm_topology_create(C.byref(h)), "hrm_topology_create")
+        self._h = h
+
+    def close(self) -> None:
+        if self._h:
+            lib().hrm_topology_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def filter2d_video(img, radius: int, topo: Topology, out=None, stream=None):
+    """Exact 2D median of one frame of a stream; the top level of the tree
+    comes from the previous frame's output held by ``topo``."""
+    _check_img(img, 2)
+    out = _torch().empty_like(img) if out is None else out
+    es = img.element_size()
+    rc = lib().hrm_filter2d_video(_dtype_code(img), img.data_ptr(), img.stride(0) * es, out.data_ptr(),
+                                  out.stride(0) * es, img.shape[1], img.shape[0], radius, topo._h,
+                                  _stream(stream))
+    check(rc, "hrm_filter2d_video")
+    return out
 
 
 class Server:

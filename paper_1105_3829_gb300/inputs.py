@@ -154,3 +154,20 @@ def request_image(req: dict) -> np.ndarray:
     if req["dtype"] == "u8":
         return uniform_u8(req["h"], req["w"], seed=req["seed"])
     return xray12_u16(req["h"], req["w"], seed=req["seed"])
+
+
+def video_frames(nframes: int = 8, h: int = 4096, w: int = 4096, drift: int = 4, seed: int | None = None):
+    """A frame stream with the low-key recipe: each frame has fresh pixel noise
+    (90 % N(2000,120), 10 % uniform 0..65535) over a smooth blob field (grid
+    in [-300, 300] at 64 px, bilinear) that drifts by ``drift`` px right and
+    down per frame.  Yields uint16 (h, w) arrays."""
+    rng = _rng(seed_for(6) if seed is None else seed)
+    pad = drift * nframes
+    field = smooth_field(rng, (h + pad, w + pad), 64, 300.0)
+    for f in range(nframes):
+        base = 2000.0 + 120.0 * rng.standard_normal((h, w), dtype=np.float32)
+        outl = rng.random((h, w), dtype=np.float32) < 0.10
+        uni = rng.integers(0, 65536, size=(h, w)).astype(np.float32)
+        o = pad - drift * f
+        val = np.where(outl, uni, base) + field[o:o + h, o:o + w]
+        yield _round_clamp(val, 65535, np.uint16)

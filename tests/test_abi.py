@@ -65,7 +65,9 @@ def test_validation_without_device(lib):
     assert hrm.hrm_filter3d(1, src, 32, 100, dst, 32, 256, 32, 8, 4, 2, 0, 0, None) == E   # slice pitch
     assert hrm.hrm_rank_filter2d(1, src, 64, dst, 64, 32, 8, 1, 9, 0, 0, None) == E        # rank >= 9
     assert hrm.hrm_filter2d_lowprec(1, src, 64, dst, 64, 32, 8, 2, 13, None) == E          # drop bits
-    assert "radius" in hrm.last_error() or "bits" in hrm.last_error()
+    assert "bits" in hrm.last_error()
+    assert hrm.hrm_filter2d_video(1, src, 64, dst, 64, 32, 8, 2, None, None) == E           # no topology
+    assert "topology" in hrm.last_error()
 
 
 def test_plan_cache_roundtrip(lib, tmp_path):
