@@ -135,16 +135,17 @@ static void size_slots(PlanH& p, int dims, int r, size_t budget) {
     p.nslots = std::max(2, std::min(slots_for(tw, r, p.cw, rest), MAX_SLOTS));
 }
 
-// Strip length: about four waves of tiles over the resident tile slots, so
-// that slow tiles (clamped windows at the image edges see noisier medians and
-// more tree nodes) even out, but at least n rows (min 96) so the per-strip
-// start-up -- building the root from n rows and the first cached nodes --
-// stays a small share of a strip.
-static int strip_length(int W, int lines, int walk, int r, int tw, size_t smem, const DeviceInfo& di) {
+// Strip length: in 2D about one wave of interior tiles over the resident
+// tile slots (the slow rows near the image edges are in short edge strips
+// that start first, see strip_layout); in 3D, where slab updates make tile
+// costs vary more, about four waves.  At least n rows (min 96) so the
+// per-strip start-up -- building the root from n rows and the first cached
+// nodes -- stays a small share of a strip.
+int strip_length(int dims, int W, int lines, int walk, int r, int tw, size_t smem, const DeviceInfo& di) {
     int bps = (int)(di.smem_per_sm / (smem + 1024));
     bps = std::max(1, std::min(bps, di.max_blocks_per_sm));
     const long tiles_x = (W + tw - 1) / tw;
-    const long target = (long)di.num_sms * bps * 4;
+    const long target = (long)di.num_sms * bps * (dims == 3 ? 4 : 1);
     long sh = (walk * tiles_x * (long)lines + target - 1) / target;
     const long n = 2L * r + 1;
     sh = std::max(sh, std::min(n, 96L));
@@ -177,14 +178,15 @@ PlanH default_plan(int dims, int es, int W, int lines, int walk, int r, const De
     p.path = ((dims == 2 && r <= SORTNET_MAX_R2D) || (dims == 3 && r == 1)) ? 1 : 2;
     p.cw = counter_width(dims, r);
     p.ppl = 1;  // 128 outputs per tile
-    // shared memory per tile: four resident tiles (16 warps, the kernel then
-    // compiled for 128 registers) per SM for medium windows, three for small
-    // and large ones (more cached nodes: rebuilds read n rows per column)
-    const int tiles_per_sm = (r >= 8 && r < 40) ? 4 : 3;
+    // shared memory per tile: four resident tiles (16 warps; the kernel is
+    // then compiled for 128 registers) per SM in 2D -- node builds over the
+    // requesting outputs' columns are cheap enough that more warps beat more
+    // cached nodes -- and in 3D for 8 <= r < 40; three otherwise
+    const int tiles_per_sm = (dims == 2 || (r >= 8 && r < 40)) ? 4 : 3;
     const size_t per_sm = (size_t)di.smem_per_sm / tiles_per_sm - 1024;
     const size_t budget = std::min((size_t)di.smem_optin, per_sm);
     size_slots(p, dims, r, budget);
-    p.sh = strip_length(W, lines, walk, r, BLOCK_THREADS * p.ppl, plan_smem(p, r), di);
+    p.sh = strip_length(dims, W, lines, walk, r, BLOCK_THREADS * p.ppl, plan_smem(p, r), di);
     return p;
 }
 
@@ -194,7 +196,7 @@ static void apply_plan(PlanH& p, const hrm_plan& hp, int dims, int W, int lines,
     if (hp.slot_kbytes > 0) size_slots(p, dims, r, (size_t)hp.slot_kbytes * 1024);
     else size_slots(p, dims, r, plan_smem(p, r));
     p.sh = hp.strip_height > 0 ? std::min(hp.strip_height, walk)
-                               : strip_length(W, lines, walk, r, BLOCK_THREADS * p.ppl, plan_smem(p, r), di);
+                               : strip_length(dims, W, lines, walk, r, BLOCK_THREADS * p.ppl, plan_smem(p, r), di);
     if (hp.path == 1 || hp.path == 2) p.path = hp.path;
 }
 

@@ -1,10 +1,10 @@
 // autotune.cu -- timed search over kernel plans for one problem class.
 //
 // Candidates: the selection network vs the histogram kernel (2D radius <= 5),
-// tile width (64/128/256 outputs per warp), shared memory per warp for the
-// node cache (which trades slots against resident warps per SM), and strip
-// length (longer strips amortise the per-tile initial build; shorter strips
-// give more tiles for load balance).  Each candidate is timed with CUDA
+// tile width (128/256 outputs per tile), shared memory per tile for the node
+// cache (which trades cached nodes against resident tiles per SM), and strip
+// length (the default one-wave length and half of it: longer strips amortise
+// the per-strip start-up, shorter ones balance slow tiles).  Each candidate is timed with CUDA
 // events on the caller's stream; the fastest is cached for the class.
 #include <cuda_runtime.h>
 
@@ -30,20 +30,6 @@ __global__ void synth_fill(unsigned char* p, size_t pitch, size_t slice, int W, 
         if (elem == 2) reinterpret_cast<uint16_t*>(row)[x] = (uint16_t)v;
         else row[x] = (unsigned char)v;
     }
-}
-
-static int strip_for(int dims, int W, int lines, int walk, int r, int tw, size_t smem, const DeviceInfo& di) {
-    int wps = (int)(di.smem_per_sm / (smem + 1024));
-    wps = std::max(1, std::min(wps, di.max_blocks_per_sm));
-    const long tiles_x = (W + tw - 1) / tw;
-    const long target = (long)di.num_sms * wps * 2;
-    long sh = (walk * tiles_x * (long)lines + target - 1) / target;
-    const long n = 2L * r + 1;
-    sh = std::max(sh, std::min(2 * n, 64L));
-    sh = std::max(sh, 8L);
-    sh = std::min(sh, (long)walk);
-    (void)dims;
-    return (int)std::max(1L, sh);
 }
 
 }  // namespace hrm
@@ -104,9 +90,9 @@ extern "C" int hrm_autotune(int dtype, int dims, int width, int height, int dept
                 if (p.nslots < 3) continue;
                 const size_t smem = plan_smem(p, radius);
                 if (smem > (size_t)di.smem_optin) continue;
-                const int sh = strip_for(dims, width, lines, walk, radius, tw, smem, di);
-                for (int f : {1, 2}) {
-                    const int shf = std::min(walk, sh * f);
+                const int sh = strip_length(dims, width, lines, walk, radius, tw, smem, di);
+                for (int f : {2, 1}) {  // the default strip length and half of it
+                    const int shf = std::max(8, sh / f);
                     if (f == 2 && shf == sh) continue;
                     cands.push_back(hrm_plan{tw, shf, kb, 2});
                 }
