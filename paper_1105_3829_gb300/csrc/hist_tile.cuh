@@ -186,12 +186,15 @@ __device__ __forceinline__ int node_digit(const Meta& m, const NodeRange& nr, ui
 }
 
 // Build the records of the m.nbuild build entries (slot, column range) at walk
-// position t (whole block): work items (entry, column) are spread over the
-// threads in column order; values come from the
-// shared-memory ring when present (2D), else from global memory with eight
-// loads in flight per thread.  The index arithmetic per value is kept to a
-// clamp and a multiply-add (no division): installs near the image corners,
-// where medians move to new nodes every row, are dominated by this loop.
+// position t (whole block).  Work items are (entry, aligned column pair):
+// both columns of a pair share the value loads (one 32-bit shared-memory load
+// from the ring in 2D, else one row address per walk step) and the index
+// arithmetic, and give two independent counting chains.  A pair may reach
+// one column outside the entry's range; that column gets its correct current
+// counts too, which is harmless (NC is even, so pairs stay inside the tile).
+// The per-value work is a clamp and a multiply-add at most (no division):
+// installs near the image corners, where medians move to new nodes every
+// row, are dominated by this loop.
 template <typename T, int CW>
 __device__ void build_slots(const HistJob& a, const Geo& g, const Meta& m, unsigned char* slots, int NC,
                             int x0, int t, const T* ring) {
@@ -202,57 +205,71 @@ __device__ void build_slots(const HistJob& a, const Geo& g, const Meta& m, unsig
     int b = 0;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         while (b + 1 < nb && (int)m.build_off[b + 1] <= it) ++b;  // items ascend per thread
-        const int cx = (int)m.build_lo[b] + (it - (int)m.build_off[b]);
+        const int c0 = 2 * (((int)m.build_lo[b] >> 1) + (it - (int)m.build_off[b]));
         const NodeRange nr = node_range(m, m.build_key[b]);
-        uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        uint32_t cnt0[8] = {0, 0, 0, 0, 0, 0, 0, 0}, cnt1[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        auto count2 = [&](uint32_t v0, uint32_t v1) {
+            const int d0 = node_digit(m, nr, v0), d1 = node_digit(m, nr, v1);
+            if (d0 >= 0) reg_count<CW>(cnt0, d0);
+            if (d1 >= 0) reg_count<CW>(cnt1, d1);
+        };
         if (ring) {
             const int M = 2 * r + 2;
             int idx = ring_idx(t - r, M);
-            const T* col = ring + cx;
+            const T* col = ring + c0;
 #pragma unroll 4
             for (int k = 0; k < n; ++k) {
-                const int d = node_digit(m, nr, (uint32_t)col[(size_t)idx * NC]);
-                if (d >= 0) reg_count<CW>(cnt, d);
+                if (sizeof(T) == 2) {
+                    const uint32_t w = *reinterpret_cast<const uint32_t*>(col + (size_t)idx * NC);
+                    count2(w & 0xFFFFu, w >> 16);
+                } else {
+                    const uint32_t w = *reinterpret_cast<const unsigned short*>(col + (size_t)idx * NC);
+                    count2(w & 0xFFu, w >> 8);
+                }
                 idx = idx + 1 == M ? 0 : idx + 1;
             }
         } else {
-            const unsigned char* base = g.src + (size_t)clampi(x0 - r + cx, 0, a.W - 1) * sizeof(T);
+            const int gx0 = clampi(x0 - r + c0, 0, a.W - 1), gx1 = clampi(x0 - r + c0 + 1, 0, a.W - 1);
             if (g.layer == 1) {  // 2D: one value per walk step
                 for (int k0 = 0; k0 < n; k0 += 8) {
-                    uint32_t v[8];
+                    uint32_t v0[8], v1[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int tc = clampi(t - r + min(k0 + u, n - 1), 0, g.tmax);
-                        v[u] = __ldg(reinterpret_cast<const T*>(base + (size_t)tc * g.tstride));
+                        const T* rp = reinterpret_cast<const T*>(g.src + (size_t)tc * g.tstride);
+                        v0[u] = __ldg(rp + gx0);
+                        v1[u] = __ldg(rp + gx1);
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         if (k0 + u >= n) break;
-                        const int d = node_digit(m, nr, v[u]);
-                        if (d >= 0) reg_count<CW>(cnt, d);
+                        count2(v0[u], v1[u]);
                     }
                 }
             } else {  // 3D: a slab of `layer` rows per walk step
                 for (int k = 0; k < n; ++k) {
-                    const unsigned char* sl = base + (size_t)clampi(t - r + k, 0, g.tmax) * g.tstride;
+                    const unsigned char* sl = g.src + (size_t)clampi(t - r + k, 0, g.tmax) * g.tstride;
                     for (int i0 = 0; i0 < g.layer; i0 += 8) {
-                        uint32_t v[8];
+                        uint32_t v0[8], v1[8];
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
                             const int ic = clampi(g.ibase + min(i0 + u, g.layer - 1), 0, g.imax);
-                            v[u] = __ldg(reinterpret_cast<const T*>(sl + (size_t)ic * g.istride));
+                            const T* rp = reinterpret_cast<const T*>(sl + (size_t)ic * g.istride);
+                            v0[u] = __ldg(rp + gx0);
+                            v1[u] = __ldg(rp + gx1);
                         }
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
                             if (i0 + u >= g.layer) break;
-                            const int d = node_digit(m, nr, v[u]);
-                            if (d >= 0) reg_count<CW>(cnt, d);
+                            count2(v0[u], v1[u]);
                         }
                     }
                 }
             }
         }
-        rec_store<CW>(slots + ((size_t)m.build_slot[b] * NC + cx) * 16 * CW, cnt);
+        unsigned char* rec = slots + ((size_t)m.build_slot[b] * NC + c0) * 16 * CW;
+        rec_store<CW>(rec, cnt0);
+        rec_store<CW>(rec + 16 * CW, cnt1);
     }
 }
 
@@ -495,7 +512,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         m.build_lo[0] = 0;
         m.build_hi[0] = (int16_t)(NC - 1);
         m.build_off[0] = 0;
-        m.build_off[1] = NC;
+        m.build_off[1] = NC / 2;  // in column pairs
         m.clo[0] = 0;
         m.chi[0] = (int16_t)(NC - 1);
     }
@@ -754,7 +771,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                                     m.build_lo[nb] = (int16_t)part_lo[q];
                                     m.build_hi[nb] = (int16_t)part_hi[q];
                                     m.build_off[nb] = off;
-                                    off += (uint32_t)(part_hi[q] - part_lo[q] + 1);
+                                    off += (uint32_t)((part_hi[q] >> 1) - (part_lo[q] >> 1) + 1);
                                     ++nb;
                                 }
                             }
