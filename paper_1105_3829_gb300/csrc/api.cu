@@ -123,7 +123,7 @@ size_t plan_smem(const PlanH& p, int r) {
 }
 
 // Fill slots (and the ring decision) for a given per-tile shared-memory budget.
-static void size_slots(PlanH& p, int dims, int r, size_t budget) {
+void size_slots(PlanH& p, int dims, int r, size_t budget) {
     const int tw = BLOCK_THREADS * p.ppl;
     const size_t ring = hist_ring_bytes(tw, r, p.es);
 #ifdef HRM_NO_RING

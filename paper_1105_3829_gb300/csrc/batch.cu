@@ -108,12 +108,12 @@ __device__ void run_item(const BatchItem& it, int tile, unsigned char* sm) {
         }
         return;
     }
-#define HRM_CASE(T, P, C) \
-    if (j.ppl == P && j.cw == C) { hist_tile<T, P, C>(j, tile, sm); return; }
+#define HRM_CASE(T, C) \
+    if (j.ppl == 1 && j.cw == C) { hist_tile<T, 1, C>(j, tile, sm); return; }
     if (j.elem == 1) {
-        HRM_CASE(uint8_t, 1, 1) HRM_CASE(uint8_t, 2, 1) HRM_CASE(uint8_t, 1, 2) HRM_CASE(uint8_t, 2, 2)
+        HRM_CASE(uint8_t, 1) HRM_CASE(uint8_t, 2)
     } else {
-        HRM_CASE(uint16_t, 1, 1) HRM_CASE(uint16_t, 2, 1) HRM_CASE(uint16_t, 1, 2) HRM_CASE(uint16_t, 2, 2)
+        HRM_CASE(uint16_t, 1) HRM_CASE(uint16_t, 2)
     }
 #undef HRM_CASE
     if (threadIdx.x == 0) set_error(j.err, DEV_BAD_JOB);
@@ -124,20 +124,25 @@ __global__ void __launch_bounds__(BLOCK_THREADS, 3) batch_kernel(const BatchItem
                                                               unsigned* counter, unsigned total) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned s_next;
+    // the current item's descriptor, staged once per tile in shared memory
+    // (a per-thread copy would live in local memory)
+    __shared__ __align__(16) BatchItem s_item;
+    static_assert(sizeof(BatchItem) % 4 == 0, "BatchItem copied as words");
     for (;;) {
         if (threadIdx.x == 0) s_next = atomicAdd(counter, 1u);
         __syncthreads();
         const unsigned t = s_next;
-        __syncthreads();  // every thread has read s_next before the next fetch
         if (t >= total) break;
         int lo = 0, hi = nitems - 1;  // last item whose first tile is <= t
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
         }
-        const BatchItem it = items[lo];
-        run_item(it, (int)(t - tile_off[lo]), smem);
-        __syncthreads();  // the tile's shared memory is free again
+        for (int i = threadIdx.x; i < (int)(sizeof(BatchItem) / 4); i += blockDim.x)
+            reinterpret_cast<uint32_t*>(&s_item)[i] = reinterpret_cast<const uint32_t*>(items + lo)[i];
+        __syncthreads();  // the descriptor is staged; every thread has read s_next
+        run_item(s_item, (int)(t - tile_off[lo]), smem);
+        __syncthreads();  // the tile's shared memory and the descriptor are free again
     }
 }
 
@@ -262,7 +267,12 @@ static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, Batch
         }
         const bool median = jb.rank < 0 || jb.rank == (N - 1) / 2;
         const uint32_t K = (uint32_t)(jb.rank < 0 ? (N + 1) / 2 : jb.rank + 1);
-        const PlanH p = resolve_plan(jb.dtype, jb.dims, im.W, im.H, im.D, jb.radius, jb.flags, di, nullptr);
+        PlanH p = resolve_plan(jb.dtype, jb.dims, im.W, im.H, im.D, jb.radius, jb.flags, di, nullptr);
+        if (p.ppl != 1) {  // the persistent kernel carries only 128-output tiles (register budget)
+            const size_t budget = plan_smem(p, jb.radius);
+            p.ppl = 1;
+            size_slots(p, jb.dims, jb.radius, budget);
+        }
         Tmp t{};
         const int es = jb.dtype == HRM_U16 ? 2 : 1;
         if (jb.dims == 2 && p.path == 1 && jb.radius <= 2 && median) {

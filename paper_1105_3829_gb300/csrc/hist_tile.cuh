@@ -249,17 +249,17 @@ __device__ void build_slots(const HistJob& a, const Geo& g, const Meta& m, unsig
             } else {  // 3D: a slab of `layer` rows per walk step
                 for (int k = 0; k < n; ++k) {
                     const unsigned char* sl = g.src + (size_t)clampi(t - r + k, 0, g.tmax) * g.tstride;
-                    for (int i0 = 0; i0 < g.layer; i0 += 8) {
-                        uint32_t v0[8], v1[8];
+                    for (int i0 = 0; i0 < g.layer; i0 += 4) {  // 8 loads in flight
+                        uint32_t v0[4], v1[4];
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
+                        for (int u = 0; u < 4; ++u) {
                             const int ic = clampi(g.ibase + min(i0 + u, g.layer - 1), 0, g.imax);
                             const T* rp = reinterpret_cast<const T*>(sl + (size_t)ic * g.istride);
                             v0[u] = __ldg(rp + gx0);
                             v1[u] = __ldg(rp + gx1);
                         }
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
+                        for (int u = 0; u < 4; ++u) {
                             if (i0 + u >= g.layer) break;
                             count2(v0[u], v1[u]);
                         }

@@ -58,6 +58,7 @@ bool plan_lookup(const ProblemKey& k, hrm_plan* p);
 void plan_store(const ProblemKey& k, const hrm_plan& p);
 // dims 2: lines = 1, walk = H; dims 3: lines = H (one tile row per y), walk = D.
 int strip_layout(int walk, int sh, int r, int* she, int* ne);
+void size_slots(PlanH& p, int dims, int r, size_t budget);
 int strip_length(int dims, int W, int lines, int walk, int r, int tw, size_t smem, const DeviceInfo& di);
 PlanH default_plan(int dims, int es, int W, int lines, int walk, int r, const DeviceInfo& di);
 PlanH resolve_plan(int dtype, int dims, int W, int H, int D, int r, unsigned flags, const DeviceInfo& di,

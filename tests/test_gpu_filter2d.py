@@ -204,3 +204,19 @@ def test_edge_strips(hrm, oracle, r, H):
             np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
         finally:
             hrm.set_plan(2, 2, 300, H, 1, r, hrm.hrm_plan(0, 0, 0, 0))
+
+
+@pytest.mark.parametrize("r", [6, 9, 14])
+def test_node_spans_widen_across_gaps(hrm, oracle, r):
+    """Alternating 40-px bands of two value populations whose phase drifts
+    down the image: a node first built for outputs at one side of a tile is
+    later wanted by outputs far away, so its column span widens across a gap."""
+    rng = np.random.default_rng(70 + r)
+    yy, xx = np.mgrid[0:160, 0:300]
+    band = ((xx + 3 * yy) // 40) % 2
+    img = np.where(band, rng.integers(1800, 2600, size=xx.shape), rng.integers(300, 900, size=xx.shape))
+    img = img.astype(np.uint16)
+    np.testing.assert_array_equal(run2d(hrm, img, r), oracle.median2d(img, r))
+    rank = (2 * r + 1) ** 2 // 3
+    out = _host(hrm.rank_filter2d(_dev(img), r, rank))
+    np.testing.assert_array_equal(out, oracle.median2d(img, r, rank=rank))
