@@ -3,7 +3,7 @@
 // capture.
 //
 // Every job is cut into the same warp tiles its single-image launch would use
-// (hierarchical-histogram strips, or selection-network tiles for radius <= 2);
+// (hierarchical-histogram strips, or selection-network tiles for 2D radius <= 5 and 3D radius 1);
 // the tiles of all jobs form one queue.  A grid of resident warps repeatedly
 // takes the next tile with an atomic counter and runs the matching tile body,
 // so small and large jobs share the GPU without per-job launches or tails.
@@ -23,7 +23,7 @@
 
 namespace hrm {
 
-enum ItemKind : int { ITEM_HIST = 0, ITEM_SORT3 = 1, ITEM_SORT5 = 2, ITEM_SORT3D = 3 };
+enum ItemKind : int { ITEM_HIST = 0, ITEM_SORT3 = 1, ITEM_SORT5 = 2, ITEM_SORT3D = 3, ITEM_SORTW = 4 };
 
 struct BatchItem {
     HistJob job;       // tile geometry, plan and rank (selection items use src/dst/pitches/W/H)
@@ -99,7 +99,15 @@ __device__ void run_item(const BatchItem& it, int tile, unsigned char* sm) {
         // a block item holds BLOCK_WARPS selection-network warp tiles
         const int wt = tile * BLOCK_WARPS + (int)(threadIdx.x >> 5);
         const int tx = wt % it.tiles_x_s, ty = wt / it.tiles_x_s;
-        if (it.kind == ITEM_SORT3) {
+        if (it.kind == ITEM_SORTW) {  // radius 3..5, pruned k x k networks (the radius is in job.r)
+#define HRM_WIDE(RR)                                                                                            \
+    if (j.r == RR) {                                                                                            \
+        if (j.elem == 1) sortnet_wide_tile<uint8_t, RR>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty); \
+        else sortnet_wide_tile<uint16_t, RR>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);      \
+    }
+            HRM_WIDE(3) HRM_WIDE(4) HRM_WIDE(5)
+#undef HRM_WIDE
+        } else if (it.kind == ITEM_SORT3) {
             if (j.elem == 1) sortnet3x3_tile<uint8_t>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);
             else sortnet3x3_tile<uint16_t>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);
         } else {
@@ -275,11 +283,14 @@ static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, Batch
         }
         Tmp t{};
         const int es = jb.dtype == HRM_U16 ? 2 : 1;
-        if (jb.dims == 2 && p.path == 1 && jb.radius <= 2 && median) {
-            t.it.kind = jb.radius == 1 ? ITEM_SORT3 : ITEM_SORT5;
+        if (jb.dims == 2 && p.path == 1 && jb.radius <= SORTNET_MAX_R2D && median) {
+            t.it.kind = jb.radius == 1 ? ITEM_SORT3 : (jb.radius == 2 ? ITEM_SORT5 : ITEM_SORTW);
             t.it.rows_per_warp = 32;
-            t.it.tiles_x_s = (im.W + 255) / 256;
+            // columns per warp tile: 256 (r <= 2), else two per output lane
+            const int tw = jb.radius <= 2 ? 256 : 2 * (32 - 2 * ((jb.radius + 1) / 2));
+            t.it.tiles_x_s = (im.W + tw - 1) / tw;
             HistJob& h = t.it.job;
+            h.r = jb.radius;
             h.src = (const unsigned char*)im.src;
             h.dst = (unsigned char*)im.dst;
             h.s_row = im.sp;
@@ -289,7 +300,7 @@ static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, Batch
             h.elem = es;
             const int wtiles = t.it.tiles_x_s * ((im.H + 31) / 32);
             h.ntiles = (wtiles + BLOCK_WARPS - 1) / BLOCK_WARPS;
-            t.cost = 1.0;
+            t.cost = jb.radius <= 2 ? 1.0 : (double)jb.radius;
         } else if (jb.dims == 3 && p.path == 1 && jb.radius == 1 && median) {
             t.it.kind = ITEM_SORT3D;
             t.it.rows_per_warp = 32;  // slices per warp tile

@@ -43,6 +43,8 @@ def mixed_jobs():
         (inputs.xray12_volume(18, 20, 64, seed=9), 2, -1, False),
         (_rand((9, 17, 33), np.uint8, 10), 1, -1, False),
         (_rand((1, 1), np.uint8, 11), 5, -1, False),
+        (inputs.xray12_u16(77, 150, seed=12), 5, -1, False),
+        (_rand((61, 211), np.uint8, 13), 4, -1, False),
     ]
 
 
