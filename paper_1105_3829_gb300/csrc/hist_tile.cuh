@@ -59,6 +59,7 @@ struct HistJob {
     int r;
     int sh;                  // strip length along the walk axis (interior strips)
     int she, ne;             // edge strips: ne strips of she steps at each end of the walk axis
+    int nint;                // interior strips (2D tile order, see hist_tile)
     int tiles_x;             // tiles across x
     int ntiles;
     uint32_t K;              // 1-based target rank
@@ -428,12 +429,36 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     const int n = 2 * r + 1;
     const int NC = TW + 2 * r;
     const int S = a.nslots;
-    const int tx = tile % a.tiles_x;
-    const int rest = tile / a.tiles_x;
-    int yrow = 0, strip = rest;
-    if (a.dims == 3) {
-        yrow = rest % a.H;
-        strip = rest / a.H;
+    // Tile order (low ids start first).  2D with two or more tile columns:
+    // the edge strips (all columns), then the interior strips' first and last
+    // tile columns -- their windows are clamped in x, so they run slower --
+    // then the other interior tiles.  3D: x fastest, then the row, then the
+    // strip.
+    int tx, yrow = 0, strip;
+    if (a.dims == 2 && a.tiles_x >= 2) {
+        const int nE = 2 * a.ne * a.tiles_x;
+        if (tile < nE) {
+            strip = tile / a.tiles_x;
+            tx = tile % a.tiles_x;
+        } else {
+            int k = tile - nE;
+            if (k < 2 * a.nint) {
+                tx = (k & 1) ? a.tiles_x - 1 : 0;
+                strip = 2 * a.ne + (k >> 1);
+            } else {
+                k -= 2 * a.nint;
+                strip = 2 * a.ne + k / (a.tiles_x - 2);
+                tx = 1 + k % (a.tiles_x - 2);
+            }
+        }
+    } else {
+        tx = tile % a.tiles_x;
+        const int rest = tile / a.tiles_x;
+        strip = rest;
+        if (a.dims == 3) {
+            yrow = rest % a.H;
+            strip = rest / a.H;
+        }
     }
     const int L = a.dims == 3 ? a.D : a.H;  // walk-axis length
     // Steps within r of either end of the walk axis see clamped windows whose
@@ -457,7 +482,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         ts = lo + (strip - 2 * a.ne) * a.sh;
         te = min(ts + a.sh, L - lo);
     }
-    if (ts >= L || x0 >= a.W) return;  // uniform across the block
+    if (ts >= L || ts >= te || x0 >= a.W) return;  // uniform across the block
 
     Geo g;
     g.src = a.src;
