@@ -135,17 +135,18 @@ void size_slots(PlanH& p, int dims, int r, size_t budget) {
     p.nslots = std::max(2, std::min(slots_for(tw, r, p.cw, rest), MAX_SLOTS));
 }
 
-// Strip length: in 2D about one wave of interior tiles over the resident
-// tile slots (the slow rows near the image edges are in short edge strips
-// that start first, see strip_layout); in 3D, where slab updates make tile
-// costs vary more, about four waves.  At least n rows (min 96) so the
+// Strip length: in 2D about two waves of interior tiles over the resident
+// tile slots for 12 <= r < 32 and one wave otherwise (measured on the x-ray
+// workload; larger windows pay more per strip start-up) (the slow rows near the image edges are in short edge
+// strips that start first, see strip_layout); in 3D, where slab updates make
+// tile costs vary more, about four waves.  At least n rows (min 96) so the
 // per-strip start-up -- building the root from n rows and the first cached
 // nodes -- stays a small share of a strip.
 int strip_length(int dims, int W, int lines, int walk, int r, int tw, size_t smem, const DeviceInfo& di) {
     int bps = (int)(di.smem_per_sm / (smem + 1024));
     bps = std::max(1, std::min(bps, di.max_blocks_per_sm));
     const long tiles_x = (W + tw - 1) / tw;
-    const long target = (long)di.num_sms * bps * (dims == 3 ? 4 : 1);
+    const long target = (long)di.num_sms * bps * (dims == 3 ? 4 : ((r >= 12 && r < 32) ? 2 : 1));
     long sh = (walk * tiles_x * (long)lines + target - 1) / target;
     const long n = 2L * r + 1;
     sh = std::max(sh, std::min(n, 96L));

@@ -568,8 +568,8 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     oc.lap(CNT_CYC_INIT);
 
     // cost model (per block): one shared prefix of a node vs direct n-column sums
-    const int prefix_cost = ((NC + NT - 1) / NT) * (CW == 1 ? 31 : 24) + 300;
-    const int direct_cost = n * (CW == 1 ? 17 : 10);
+    const int prefix_cost = ((NC + NT - 1) / NT) * (CW == 1 ? 31 : 24) + 700;  // incl. two barriers
+    const int direct_cost = n * (CW == 1 ? 24 : 14);
     uint32_t pass_id = 0;
 
     for (int t = ts; t < te; ++t) {
