@@ -138,15 +138,15 @@ void size_slots(PlanH& p, int dims, int r, size_t budget) {
 // Strip length: in 2D about two waves of interior tiles over the resident
 // tile slots for 12 <= r < 32 and one wave otherwise (measured on the x-ray
 // workload; larger windows pay more per strip start-up) (the slow rows near the image edges are in short edge
-// strips that start first, see strip_layout); in 3D, where slab updates make
-// tile costs vary more, about four waves.  At least n rows (min 96) so the
+// strips that start first, see strip_layout); in 3D about two waves for
+// 5 <= r < 8 and four otherwise (measured on the 256^3 volume).  At least n rows (min 96) so the
 // per-strip start-up -- building the root from n rows and the first cached
 // nodes -- stays a small share of a strip.
 int strip_length(int dims, int W, int lines, int walk, int r, int tw, size_t smem, const DeviceInfo& di) {
     int bps = (int)(di.smem_per_sm / (smem + 1024));
     bps = std::max(1, std::min(bps, di.max_blocks_per_sm));
     const long tiles_x = (W + tw - 1) / tw;
-    const long target = (long)di.num_sms * bps * (dims == 3 ? 4 : ((r >= 12 && r < 32) ? 2 : 1));
+    const long target = (long)di.num_sms * bps * (dims == 3 ? ((r >= 5 && r < 8) ? 2 : 4) : ((r >= 12 && r < 32) ? 2 : 1));
     long sh = (walk * tiles_x * (long)lines + target - 1) / target;
     const long n = 2L * r + 1;
     sh = std::max(sh, std::min(n, 96L));
@@ -182,8 +182,8 @@ PlanH default_plan(int dims, int es, int W, int lines, int walk, int r, const De
     // shared memory per tile: four resident tiles (16 warps; the kernel is
     // then compiled for 128 registers) per SM in 2D -- node builds over the
     // requesting outputs' columns are cheap enough that more warps beat more
-    // cached nodes -- and in 3D for 8 <= r < 40; three otherwise
-    const int tiles_per_sm = (dims == 2 || (r >= 8 && r < 40)) ? 4 : 3;
+    // cached nodes -- and in 3D for 5 <= r < 40; three otherwise
+    const int tiles_per_sm = (dims == 2 || (r >= 5 && r < 40)) ? 4 : 3;
     const size_t per_sm = (size_t)di.smem_per_sm / tiles_per_sm - 1024;
     const size_t budget = std::min((size_t)di.smem_optin, per_sm);
     size_slots(p, dims, r, budget);

@@ -18,20 +18,12 @@
 #include <type_traits>
 #include <vector>
 
+#include "batch_kernel.cuh"
 #include "runtime.h"
-#include "sortnet.cuh"
 
 namespace hrm {
 
-enum ItemKind : int { ITEM_HIST = 0, ITEM_SORT3 = 1, ITEM_SORT5 = 2, ITEM_SORT3D = 3, ITEM_SORTW = 4 };
 
-struct BatchItem {
-    HistJob job;       // tile geometry, plan and rank (selection items use src/dst/pitches/W/H)
-    int kind;
-    int rows_per_warp; // selection-network tiles
-    int tiles_x_s;     // selection-network tiles across
-    int pad;
-};
 
 // Level pre-pass for many images at once (uniform trees need only the value range).
 struct LevelItem {
@@ -77,80 +69,6 @@ __global__ void batch_minmax(const LevelItem* items, int n) {
     if (lane == 0) {
         atomicMin(&it.desc->vmin, lo);
         atomicMax(&it.desc->vmax, hi);
-    }
-}
-
-__device__ void run_item(const BatchItem& it, int tile, unsigned char* sm) {
-    const HistJob& j = it.job;
-    if (it.kind == ITEM_SORT3D) {
-        // warp tiles: 256 columns x one row x rows_per_warp slices
-        const int wt = tile * BLOCK_WARPS + (int)(threadIdx.x >> 5);
-        const int tx = wt % it.tiles_x_s, rest = wt / it.tiles_x_s;
-        const int y = rest % j.H, tz = rest / j.H;
-        if (j.elem == 1)
-            sortnet3d_tile<uint8_t>(j.src, j.s_row, j.s_slice, j.dst, j.d_row, j.d_slice, j.W, j.H, j.D,
-                                    it.rows_per_warp, tx, y, tz);
-        else
-            sortnet3d_tile<uint16_t>(j.src, j.s_row, j.s_slice, j.dst, j.d_row, j.d_slice, j.W, j.H, j.D,
-                                     it.rows_per_warp, tx, y, tz);
-        return;
-    }
-    if (it.kind != ITEM_HIST) {
-        // a block item holds BLOCK_WARPS selection-network warp tiles
-        const int wt = tile * BLOCK_WARPS + (int)(threadIdx.x >> 5);
-        const int tx = wt % it.tiles_x_s, ty = wt / it.tiles_x_s;
-        if (it.kind == ITEM_SORTW) {  // radius 3..5, pruned k x k networks (the radius is in job.r)
-#define HRM_WIDE(RR)                                                                                            \
-    if (j.r == RR) {                                                                                            \
-        if (j.elem == 1) sortnet_wide_tile<uint8_t, RR>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty); \
-        else sortnet_wide_tile<uint16_t, RR>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);      \
-    }
-            HRM_WIDE(3) HRM_WIDE(4) HRM_WIDE(5)
-#undef HRM_WIDE
-        } else if (it.kind == ITEM_SORT3) {
-            if (j.elem == 1) sortnet3x3_tile<uint8_t>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);
-            else sortnet3x3_tile<uint16_t>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);
-        } else {
-            if (j.elem == 1) sortnet5x5_tile<uint8_t>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);
-            else sortnet5x5_tile<uint16_t>(j.src, j.s_row, j.dst, j.d_row, j.W, j.H, it.rows_per_warp, tx, ty);
-        }
-        return;
-    }
-#define HRM_CASE(T, C) \
-    if (j.ppl == 1 && j.cw == C) { hist_tile<T, 1, C>(j, tile, sm); return; }
-    if (j.elem == 1) {
-        HRM_CASE(uint8_t, 1) HRM_CASE(uint8_t, 2)
-    } else {
-        HRM_CASE(uint16_t, 1) HRM_CASE(uint16_t, 2)
-    }
-#undef HRM_CASE
-    if (threadIdx.x == 0) set_error(j.err, DEV_BAD_JOB);
-}
-
-__global__ void __launch_bounds__(BLOCK_THREADS, 3) batch_kernel(const BatchItem* __restrict__ items,
-                                                              const unsigned* __restrict__ tile_off, int nitems,
-                                                              unsigned* counter, unsigned total) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned s_next;
-    // the current item's descriptor, staged once per tile in shared memory
-    // (a per-thread copy would live in local memory)
-    __shared__ __align__(16) BatchItem s_item;
-    static_assert(sizeof(BatchItem) % 4 == 0, "BatchItem copied as words");
-    for (;;) {
-        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1u);
-        __syncthreads();
-        const unsigned t = s_next;
-        if (t >= total) break;
-        int lo = 0, hi = nitems - 1;  // last item whose first tile is <= t
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
-        }
-        for (int i = threadIdx.x; i < (int)(sizeof(BatchItem) / 4); i += blockDim.x)
-            reinterpret_cast<uint32_t*>(&s_item)[i] = reinterpret_cast<const uint32_t*>(items + lo)[i];
-        __syncthreads();  // the descriptor is staged; every thread has read s_next
-        run_item(s_item, (int)(t - tile_off[lo]), smem);
-        __syncthreads();  // the tile's shared memory and the descriptor are free again
     }
 }
 
@@ -393,14 +311,22 @@ static int enqueue_batch(const Plan& bp, const BatchDev& dev, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_fail(e, "batch counter reset");
     const size_t smem = bp.smem;
     if (smem > (size_t)di.smem_optin) return fail(HRM_ENOTSUP, "batch plan exceeds shared memory");
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e, "batch smem attribute");
-    }
     int per_sm = std::max(1, std::min(di.max_blocks_per_sm, (int)(di.smem_per_sm / (smem + 1024))));
-    unsigned grid = (unsigned)std::min<long>((long)di.num_sms * per_sm, (long)bp.total);
-    batch_kernel<<<grid, BLOCK_THREADS, smem, st>>>(dev.items, dev.offs, (int)bp.items.size(), dev.counter, bp.total);
-    e = cudaGetLastError();
+    if (per_sm >= 4) {  // four tiles fit: the 128-register instantiation
+        per_sm = 4;
+        const unsigned grid = (unsigned)std::min<long>((long)di.num_sms * per_sm, (long)bp.total);
+        e = launch_batch_kernel4(grid, smem, st, dev.items, dev.offs, (int)bp.items.size(), dev.counter, bp.total);
+    } else {
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(batch_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_fail(e, "batch smem attribute");
+        }
+        per_sm = std::min(per_sm, 3);
+        const unsigned grid = (unsigned)std::min<long>((long)di.num_sms * per_sm, (long)bp.total);
+        batch_kernel<3><<<grid, BLOCK_THREADS, smem, st>>>(dev.items, dev.offs, (int)bp.items.size(), dev.counter,
+                                                           bp.total);
+        e = cudaGetLastError();
+    }
     return e == cudaSuccess ? HRM_OK : cuda_fail(e, "batch kernel launch");
 }
 
