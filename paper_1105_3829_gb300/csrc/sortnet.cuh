@@ -20,7 +20,9 @@
 // r = 3..5: the same pruning for the general k x k block (k = 2r+1), with
 //        one column pair per lane and the neighbouring columns fetched by
 //        shuffles one rank-row at a time (register footprint ~ the
-//        candidate count: 29, 47, 73 for k = 7, 9, 11).
+//        candidate count: 29, 47, 73 for k = 7, 9, 11); the candidates of
+//        each rank-row form a sorted run, and the runs are merged pairwise
+//        down to the selected position.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
