@@ -123,16 +123,17 @@ def csrc_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str):
-    """DRAM bytes per launch recorded by profiles/traffic.json for the current
-    kernel sources (null when the sources changed since the capture)."""
+def traffic_for(kernel: str, key: str = "kernels"):
+    """Per-launch figures recorded by profiles/traffic.json for the current
+    kernel sources (DRAM bytes by default; null when the sources changed
+    since the capture)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("csrc_hash") != csrc_hash():
         return None
-    return d.get("kernels", {}).get(kernel)
+    return d.get(key, {}).get(kernel)
 
 
 # ---- multi-GPU host logic (weak scaling: every rank filters its own image) ----
@@ -630,6 +631,10 @@ def report(args, ws, times, dev_ms_step, value, t_wall, e2e_ms, clk, npx, dist, 
         "roofline": {"bound": "hbm", "kernel": kname + " (the hrm_filter2d call: level pre-pass + kernel)",
                      "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
                      "peak_kind": peak_kind, "traffic": traffic_for(kname),
+                     "ncu_issue_active": traffic_for(kname, "issue_active"),
+                     "ncu_alu_pipe_active": traffic_for(kname, "alu_pipe_active"),
+                     "note": "the histogram kernel (r >= 6) is limited by instruction issue and latency, "
+                             "not by HBM; ncu_issue_active is its measured issue utilisation",
                      "algorithmic_bytes_per_launch": 4 * npx},
         "gpu_launches": launches_per_step * args.steps,
         "e2e": None if e2e_ms != e2e_ms else
