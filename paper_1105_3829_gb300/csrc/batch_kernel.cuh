@@ -55,8 +55,12 @@ __device__ __forceinline__ void run_item(const BatchItem& it, int tile, unsigned
         }
         return;
     }
-#define HRM_CASE(T, C) \
-    if (j.ppl == 1 && j.cw == C) { hist_tile<T, 1, C>(j, tile, sm); return; }
+#define HRM_CASE(T, C)                                                          \
+    if (j.ppl == 1 && j.cw == C) {                                              \
+        if (j.dims == 3) hist_tile<T, 1, C, 3>(j, tile, sm);                    \
+        else hist_tile<T, 1, C, 2>(j, tile, sm);                                \
+        return;                                                                 \
+    }
     if (j.elem == 1) {
         HRM_CASE(uint8_t, 1) HRM_CASE(uint8_t, 2)
     } else {

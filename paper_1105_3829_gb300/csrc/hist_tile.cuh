@@ -196,7 +196,7 @@ __device__ __forceinline__ int node_digit(const Meta& m, const NodeRange& nr, ui
 // The per-value work is a clamp and a multiply-add at most (no division):
 // installs near the image corners, where medians move to new nodes every
 // row, are dominated by this loop.
-template <typename T, int CW>
+template <typename T, int CW, int DIMS>
 __device__ void build_slots(const HistJob& a, const Geo& g, const Meta& m, unsigned char* slots, int NC,
                             int x0, int t, const T* ring) {
     const int r = a.r;
@@ -231,7 +231,7 @@ __device__ void build_slots(const HistJob& a, const Geo& g, const Meta& m, unsig
             }
         } else {
             const int gx0 = clampi(x0 - r + c0, 0, a.W - 1), gx1 = clampi(x0 - r + c0 + 1, 0, a.W - 1);
-            if (g.layer == 1) {  // 2D: one value per walk step
+            if (DIMS == 2) {  // one value per walk step
                 for (int k0 = 0; k0 < n; k0 += 8) {
                     uint32_t v0[8], v1[8];
 #pragma unroll
@@ -420,7 +420,7 @@ __device__ __forceinline__ void note_used(Meta::Round& rb, const int (&slot)[PPL
     }
 }
 
-template <typename T, int PPL, int CW>
+template <typename T, int PPL, int CW, int DIMS>
 __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     constexpr int NT = BLOCK_THREADS;
     constexpr int TW = NT * PPL;
@@ -435,7 +435,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     // then the other interior tiles.  3D: x fastest, then the row, then the
     // strip.
     int tx, yrow = 0, strip;
-    if (a.dims == 2 && a.tiles_x >= 2) {
+    if (DIMS == 2 && a.tiles_x >= 2) {
         const int nE = 2 * a.ne * a.tiles_x;
         if (tile < nE) {
             strip = tile / a.tiles_x;
@@ -455,12 +455,12 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         tx = tile % a.tiles_x;
         const int rest = tile / a.tiles_x;
         strip = rest;
-        if (a.dims == 3) {
+        if (DIMS == 3) {
             yrow = rest % a.H;
             strip = rest / a.H;
         }
     }
-    const int L = a.dims == 3 ? a.D : a.H;  // walk-axis length
+    const int L = DIMS == 3 ? a.D : a.H;  // walk-axis length
     // Steps within r of either end of the walk axis see clamped windows whose
     // medians are much noisier (more tree nodes per row; near the image
     // corners several times the work of an interior step).  They come first
@@ -486,7 +486,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
 
     Geo g;
     g.src = a.src;
-    if (a.dims == 3) {
+    if (DIMS == 3) {
         g.tstride = a.s_slice;
         g.istride = a.s_row;
         g.tmax = a.D - 1;
@@ -501,13 +501,13 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         g.ibase = 0;
         g.layer = 1;
     }
-    unsigned char* drow0 = a.dst + (a.dims == 3 ? (size_t)yrow * a.d_row : 0);
-    const size_t dstep = a.dims == 3 ? a.d_slice : a.d_row;
+    unsigned char* drow0 = a.dst + (DIMS == 3 ? (size_t)yrow * a.d_row : 0);
+    const size_t dstep = DIMS == 3 ? a.d_slice : a.d_row;
 
     Meta& m = *reinterpret_cast<Meta*>(sm);
     uint4* pfx = reinterpret_cast<uint4*>(sm + META_BYTES);
     unsigned char* slots = sm + META_BYTES + (size_t)(NC + 1) * 32;
-    const bool use_ring = a.ring && a.dims == 2 && CW == 1;
+    const bool use_ring = a.ring && DIMS == 2 && CW == 1;
     T* ring = use_ring ? reinterpret_cast<T*>(slots + (size_t)S * NC * 16 * CW) : nullptr;
     const int M = 2 * r + 2;  // ring rows
     // the thread's columns cx = tid + NT*j, j < CPL, cover NC <= TW + 2*127
@@ -542,7 +542,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         m.chi[0] = (int16_t)(NC - 1);
     }
     __syncthreads();
-    build_slots<T, CW>(a, g, m, slots, NC, x0, ts, ring);
+    build_slots<T, CW, DIMS>(a, g, m, slots, NC, x0, ts, ring);
     __syncthreads();
     if (tid == 0) m.nbuild = 0;
 
@@ -550,7 +550,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     // step are loaded one step ahead, so their latency hides behind the walk.
     uint32_t nin[CPL], nout[CPL];
     auto prefetch = [&](int tn) {
-        if (a.dims != 2 || tn >= te) return;
+        if (DIMS != 2 || tn >= te) return;
         const int ti = clampi(tn + r, 0, L - 1), to = clampi(tn - r - 1, 0, L - 1);
         const T* rin = reinterpret_cast<const T*>(a.src + (size_t)ti * a.s_row);
         const T* rout = reinterpret_cast<const T*>(a.src + (size_t)to * a.s_row);
@@ -577,7 +577,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         if (t > ts) {
             const int to = clampi(t - r - 1, 0, L - 1);
             const int ti = clampi(t + r, 0, L - 1);
-            if (a.dims == 2 && CW == 1) {
+            if (DIMS == 2 && CW == 1) {
                 T* rin = use_ring ? ring + (size_t)ring_idx(t + r, M) * NC : nullptr;
                 const T* rout = use_ring ? ring + (size_t)ring_idx(t - r - 1, M) * NC : nullptr;
                 // root level: each of the thread's column records is read,
@@ -817,7 +817,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                     }
                     __syncthreads();
                     oc.lap(CNT_CYC_ALLOC);
-                    build_slots<T, CW>(a, g, m, slots, NC, x0, t, ring);
+                    build_slots<T, CW, DIMS>(a, g, m, slots, NC, x0, t, ring);
                     oc.add(CNT_INSTALLS, m.nbuild);
                     bool got[PPL];
 #pragma unroll
