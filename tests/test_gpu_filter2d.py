@@ -220,3 +220,25 @@ def test_node_spans_widen_across_gaps(hrm, oracle, r):
     rank = (2 * r + 1) ** 2 // 3
     out = _host(hrm.rank_filter2d(_dev(img), r, rank))
     np.testing.assert_array_equal(out, oracle.median2d(img, r, rank=rank))
+
+
+def test_autotune_plans_keep_parity(hrm, oracle):
+    """hrm_autotune times candidate plans on the image and caches the fastest;
+    whatever it picks, the output stays the exact median."""
+    from paper_1105_3829_gb300 import inputs
+    img = inputs.lowkey16_u16(180, 420, seed=31)
+    src = _dev(img)
+    for r, adaptive in ((3, False), (9, False), (9, True), (24, False)):
+        plan = hrm.autotune(src, r, adaptive=adaptive)
+        assert plan.path in (1, 2)
+        assert plan.tile_width in (0, 128, 256)
+        got = hrm.get_plan(2, 2, 420, 180, 1, r, adaptive=adaptive)
+        assert (got.tile_width, got.strip_height, got.slot_kbytes, got.path) == \
+            (plan.tile_width, plan.strip_height, plan.slot_kbytes, plan.path)
+        out = _host(hrm.filter2d(src, r, adaptive=adaptive))
+        np.testing.assert_array_equal(out, oracle.median2d(img, r))
+    vol = inputs.xray12_volume(20, 24, 70, seed=3)
+    vsrc = _dev(vol)
+    hrm.autotune(vsrc, 3)
+    out = _host(hrm.filter3d(vsrc, 3))
+    np.testing.assert_array_equal(out, oracle.median3d(vol, 3))
