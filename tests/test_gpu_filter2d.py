@@ -242,3 +242,21 @@ def test_autotune_plans_keep_parity(hrm, oracle):
     hrm.autotune(vsrc, 3)
     out = _host(hrm.filter3d(vsrc, 3))
     np.testing.assert_array_equal(out, oracle.median3d(vol, 3))
+
+
+def test_very_large_image_sampled(hrm, oracle):
+    """A 12288 x 16384 uint16 image (384 MiB in, 384 MiB out): index
+    arithmetic beyond 2^31 bytes of addressed data, sampled against the oracle."""
+    rng = np.random.default_rng(77)
+    H, W = 12288, 16384
+    img = rng.integers(0, 4096, size=(H, W), dtype=np.uint16)
+    src = _dev(img)
+    for r in (2, 7, 40):
+        out = hrm.filter2d(src, r)
+        hrm.device_status()
+        ys = np.concatenate([rng.integers(0, H, 200), [0, H - 1, 0, H - 1]])
+        xs = np.concatenate([rng.integers(0, W, 200), [0, 0, W - 1, W - 1]])
+        got = out.view(torch.int16)[torch.from_numpy(ys).cuda(), torch.from_numpy(xs).cuda()]
+        got = got.cpu().numpy().view(np.uint16)  # (CUDA indexing has no uint16 kernel)
+        np.testing.assert_array_equal(got, oracle.points(img, r, ys, xs))
+        del out
