@@ -202,19 +202,24 @@ int hrm_batch_graph_destroy(hrm_batch_graph* g);
 /* ---- planning / autotuning ---------------------------------------------
  *
  * The hierarchical kernels are parameterised by tile width (output columns
- * per warp), strip length (rows or slices walked per tile) and the shared
- * memory per warp for cached tree nodes.  hrm_autotune times candidate plans
+ * per 4-warp tile), strip length (rows or slices walked per tile) and the
+ * shared memory per tile for cached tree nodes.  hrm_autotune times candidate plans
  * for one problem class on `stream` and caches the fastest; later calls of
  * the same class (dtype, dims, size, radius, flags) use it.  The timing runs
  * on `sample` (device pointer, the caller's pitches) when it is not NULL --
  * speed depends on the data, so a representative image is best -- and on a
  * synthetic image otherwise.  hrm_autotune allocates and frees its own output
  * (and synthetic input) buffers and blocks until the timing finishes.  The
- * cache is per process; hrm_plan_save / hrm_plan_load persist it as text. */
+ * cache is per process; hrm_plan_save / hrm_plan_load persist it as text.
+ * Environment, read once per process: HRM_PLAN_CACHE=<file> loads a saved
+ * plan file before the first call (a missing or malformed file is ignored);
+ * HRM_FORCE_PATH=hist or =sortnet forces the histogram kernel or the
+ * selection networks (where one exists for the problem) in every call
+ * without an explicit plan.  Outputs never depend on the plan. */
 typedef struct {
-    int tile_width;     /* output columns per warp tile: 64, 128 or 256      */
-    int strip_height;   /* output rows (2D) or slices (3D) per tile           */
-    int slot_kbytes;    /* shared memory per warp for the tree nodes (KB)     */
+    int tile_width;     /* output columns per tile: 128 or 256 (0 = default) */
+    int strip_height;   /* output rows (2D) or slices (3D) per tile (0 = default) */
+    int slot_kbytes;    /* shared memory per tile, KB (0 = default)            */
     int path;           /* 0 = auto, 1 = selection network, 2 = histogram     */
 } hrm_plan;
 

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <map>
@@ -93,7 +94,33 @@ static std::map<std::tuple<int, int, int, int, int, int, unsigned>, hrm_plan> g_
 static std::tuple<int, int, int, int, int, int, unsigned> tkey(const ProblemKey& k) {
     return std::make_tuple(k.dtype, k.dims, k.width, k.height, k.depth, k.radius, k.flags);
 }
+// Environment (read once per process): HRM_PLAN_CACHE=<file> loads saved
+// plans (hrm_plan_save format) before the first lookup; HRM_FORCE_PATH=hist
+// or =sortnet forces the histogram kernel or the selection networks (where a
+// network exists for the problem) for every call.
+static void env_plans_once() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char* f = std::getenv("HRM_PLAN_CACHE");
+        if (f && *f) {
+            if (hrm_plan_load(f) != HRM_OK) clear_error();  // a missing or bad file leaves the defaults
+        }
+    });
+}
+
+static int env_forced_path() {
+    static const int v = [] {
+        const char* s = std::getenv("HRM_FORCE_PATH");
+        if (!s) return 0;
+        if (!std::strcmp(s, "sortnet")) return 1;
+        if (!std::strcmp(s, "hist")) return 2;
+        return 0;
+    }();
+    return v;
+}
+
 bool plan_lookup(const ProblemKey& k, hrm_plan* p) {
+    env_plans_once();
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_plans.find(tkey(k));
     if (it == g_plans.end()) return false;
@@ -210,6 +237,7 @@ PlanH resolve_plan(int dtype, int dims, int W, int H, int D, int r, unsigned fla
     hrm_plan hp;
     if (plan_lookup(ProblemKey{dtype, dims, W, H, D, r, flags}, &hp)) apply_plan(p, hp, dims, W, lines, walk, r, di);
     if (force) apply_plan(p, *force, dims, W, lines, walk, r, di);
+    else if (env_forced_path()) p.path = env_forced_path();
     // the shared-memory plan must fit the device
     while (p.nslots > 2 && plan_smem(p, r) > (size_t)di.smem_optin) --p.nslots;
     if (plan_smem(p, r) > (size_t)di.smem_optin) p.ring = 0;

@@ -92,3 +92,27 @@ def test_batch_rejects_malformed_jobs(lib):
     jobs = (hrm.hrm_job * 1)()
     assert hrm.hrm_filter_batch(jobs, -1, None) == hrm.HRM_EINVAL
     assert hrm.hrm_filter_batch(jobs, 0, None) == hrm.HRM_OK
+
+
+def test_environment_plan_cache_and_forced_path(lib, tmp_path):
+    """HRM_PLAN_CACHE preloads a saved plan file; HRM_FORCE_PATH picks the
+    kernel family for calls without an explicit plan (checked in fresh
+    processes: both are read once per process)."""
+    import subprocess
+    import sys
+    plans = tmp_path / "plans.txt"
+    plans.write_text("# saved\n2 2 640 480 1 9 0 256 40 60 2\n")
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1105_3829_gb300 import hrm\n"
+            "p = hrm.get_plan(2, 2, 640, 480, 1, 9)\n"
+            "q = hrm.get_plan(2, 2, 640, 480, 1, 3)\n"
+            "print(p.tile_width, p.strip_height, p.slot_kbytes, p.path, q.path)\n") % ROOT
+    env = dict(os.environ, HRM_PLAN_CACHE=str(plans), HRM_FORCE_PATH="hist", CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert out.stdout.split() == ["256", "40", "60", "2", "2"]
+    env = dict(os.environ, HRM_FORCE_PATH="sortnet", CUDA_VISIBLE_DEVICES="")
+    env.pop("HRM_PLAN_CACHE", None)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert out.stdout.split()[3:] == ["1", "1"]
