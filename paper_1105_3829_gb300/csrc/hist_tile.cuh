@@ -835,7 +835,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                     note_used<PPL>(rb, slot, got, tid, NT);
                     __syncthreads();  // new records built, all spans recorded
                 }
-                {
+                if (PPL > 1) {
                     const unsigned wmax = __reduce_max_sync(0xffffffffu, (unsigned)nres);
                     if (wmax && lane == 0) atomicMax(&rb.maxres, wmax);
                 }
@@ -846,9 +846,13 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                 for (int k = 0; k < PPL; ++k) res[k] = todo[k] && slot[k] >= 0;
                 const uint32_t used = rb.used;
                 const int groups = __popc(used);
-                // maxres is complete only after a barrier; the prefix path does not need it
+                // With one output per thread every thread with a resolved output
+                // has exactly one, so the decision needs no barrier; otherwise
+                // maxres is complete only after one (the prefix path needs none).
                 bool direct = false;
-                if (n * (CW == 1 ? 17 : 10) < groups * prefix_cost) {
+                if (PPL == 1) {
+                    direct = groups > 0 && direct_cost < groups * prefix_cost;
+                } else if (n * (CW == 1 ? 24 : 14) < groups * prefix_cost) {
                     __syncthreads();
                     direct = (int)rb.maxres * direct_cost < groups * prefix_cost;
                 }
