@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define HRM_VERSION 100 /* 1.0.0 */
+#define HRM_VERSION 110 /* 1.1.0 */
 
 typedef enum { HRM_U8 = 1, HRM_U16 = 2 } hrm_dtype;
 
@@ -138,12 +138,26 @@ int hrm_filter2d_lowprec(int dtype, const void* src, size_t src_pitch, void* dst
  * stream: calls that share a topology must be ordered (one stream, or events),
  * and the topology must outlive them.  create: HRM_ENOMEM if the allocation
  * fails.  video: HRM_EINVAL for a null topology or one created on another
- * device, plus hrm_filter2d's argument errors. */
+ * device, plus hrm_filter2d's argument errors.  Frames also run inside
+ * batches (hrm_job.topo) and through the serving loop (hrm_request.topo). */
 typedef struct hrm_topology hrm_topology;
 int hrm_topology_create(hrm_topology** out);
 int hrm_topology_destroy(hrm_topology* topo);
 int hrm_filter2d_video(int dtype, const void* src, size_t src_pitch, void* dst, size_t dst_pitch,
                        int width, int height, int radius, hrm_topology* topo, void* stream);
+
+/* The top level a topology currently holds (what the next frame will use).
+ * dtype = 0 until a frame has been filtered with it.  mode 1: the 16 top
+ * intervals are [edge[i], edge[i+1]), edge[16] = vmax + 1; mode 0: the
+ * uniform tree over [0, vmax] (edge[] all 0).  Waits for `stream` (the one
+ * the topology's last frame ran on) before reading the device state.
+ * HRM_EINVAL for a null argument. */
+typedef struct {
+    int dtype;
+    unsigned mode, vmin, vmax;
+    unsigned edge[17];
+} hrm_topology_info;
+int hrm_topology_get(hrm_topology* topo, void* stream, hrm_topology_info* out);
 
 /* ---- batched form: many images of uneven size and radius, one launch ----
  *
@@ -151,7 +165,13 @@ int hrm_filter2d_video(int dtype, const void* src, size_t src_pitch, void* dst, 
  * level pre-passes) over a device tile work queue: each resident warp
  * repeatedly takes the next (job, tile) work item until the queue is empty.
  * Jobs may mix dtype, dims, size and radius.  Outputs are bit-identical to
- * the corresponding single-image calls. */
+ * the corresponding single-image calls.  A job with a topology is one frame
+ * of that stream: its top level comes from the topology (or from its own
+ * adaptive pre-pass when the topology holds none of its dtype) and its output
+ * becomes the topology's next estimate after the launch; a topology may
+ * appear in at most one job per call (HRM_EINVAL otherwise), and a graph
+ * (hrm_batch_graph_create) takes topology jobs only once each topology holds
+ * a top level of its job's dtype. */
 typedef struct {
     int dtype;              /* HRM_U8 / HRM_U16                               */
     int dims;               /* 2 or 3                                          */
@@ -165,6 +185,8 @@ typedef struct {
     int radius;
     long rank;              /* -1 = median, else 0-based order statistic       */
     unsigned flags;         /* 0 or HRM_ADAPTIVE                               */
+    hrm_topology* topo;     /* NULL, or a frame stream: 2D median, flags 0;   */
+                            /* the job runs as hrm_filter2d_video would       */
 } hrm_job;
 
 int hrm_filter_batch(const hrm_job* jobs, int njobs, void* stream);
@@ -242,7 +264,12 @@ int hrm_plan_load(const char* path);
  * request's tiles join the next persistent-kernel wave, so requests that
  * arrive while others run are added as memory and slots free up.  A
  * background host thread drives copies and waves on the server's own
- * streams. */
+ * streams.  Frame streams (Section III-C, previous frame as the median
+ * estimate): requests that name the same topology are filtered in submission
+ * order, each with the top level left by the one before it; two frames of one
+ * stream never share a wave (the later one waits for the next), and a wave
+ * on the other compute stream waits for the wave that last used the
+ * topology.  The topology must outlive its requests. */
 typedef struct hrm_server hrm_server;
 
 typedef struct {
@@ -256,6 +283,8 @@ typedef struct {
     size_t dst_pitch;
     int src_on_host;          /* 1: src is host memory (pinned is fastest)     */
     int dst_on_host;          /* 1: dst is host memory                         */
+    hrm_topology* topo;       /* NULL, or the frame stream this frame belongs  */
+                              /* to (flags must then be 0)                     */
 } hrm_request;
 
 typedef struct {

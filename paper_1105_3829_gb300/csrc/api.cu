@@ -377,6 +377,24 @@ int filter_impl(const Image& im, int r, long rank, unsigned flags, int drop_bits
     return e == cudaSuccess ? HRM_OK : cuda_fail(e, "hist launch");
 }
 
+int topology_check(const hrm_topology* t) {
+    if (!t) return fail(HRM_EINVAL, "null topology");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != t->device) return fail(HRM_EINVAL, "topology belongs to another device");
+    return HRM_OK;
+}
+
+int topology_device_of(const hrm_topology* t) { return t->device; }
+
+int topology_update(hrm_topology* t, int dtype, const void* dst, size_t dp, int W, int H, cudaStream_t st) {
+    const cudaError_t e = launch_topology_from_output(dtype == HRM_U16 ? 2 : 1, dst, dp, W, H, t->desc, t->hist,
+                                                      device_info().num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(e, "topology update launch");
+    t->dtype = dtype;
+    return HRM_OK;
+}
+
 }  // namespace hrm
 
 using namespace hrm;
@@ -437,13 +455,6 @@ int hrm_filter2d_lowprec(int dtype, const void* src, size_t src_pitch, void* dst
     return filter_impl(im, radius, -1, 0, drop_bits, &force, (cudaStream_t)stream);
 }
 
-struct hrm_topology {
-    int device = -1;
-    int dtype = 0;      // dtype of the frame the descriptor was made from (0: none yet)
-    LevelDesc* desc = nullptr;
-    uint32_t* hist = nullptr;
-};
-
 int hrm_topology_create(hrm_topology** out) {
     if (!out) return fail(HRM_EINVAL, "null topology pointer");
     *out = nullptr;
@@ -473,22 +484,34 @@ int hrm_topology_destroy(hrm_topology* t) {
 
 int hrm_filter2d_video(int dtype, const void* src, size_t src_pitch, void* dst, size_t dst_pitch, int width,
                        int height, int radius, hrm_topology* topo, void* stream) {
-    if (!topo) return fail(HRM_EINVAL, "null topology");
-    int dev = -1;
-    cudaGetDevice(&dev);
-    if (dev != topo->device) return fail(HRM_EINVAL, "topology belongs to another device");
+    int rc = topology_check(topo);
+    if (rc) return rc;
     Image im{dtype, 2, src, dst, src_pitch, 0, dst_pitch, 0, width, height, 1};
-    int rc = validate(im, radius, HRM_BORDER_REPLICATE, 0);
+    rc = validate(im, radius, HRM_BORDER_REPLICATE, 0);
     if (rc) return rc;
     if (width == 0 || height == 0) return HRM_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const LevelDesc* given = topo->dtype == dtype ? topo->desc : nullptr;
     rc = filter_impl(im, radius, -1, given ? 0u : (unsigned)HRM_ADAPTIVE, 0, nullptr, st, given);
     if (rc) return rc;
-    const cudaError_t e = launch_topology_from_output(dtype == HRM_U16 ? 2 : 1, dst, dst_pitch, width, height,
-                                                      topo->desc, topo->hist, device_info().num_sms, st);
-    if (e != cudaSuccess) return cuda_fail(e, "topology update launch");
-    topo->dtype = dtype;
+    return topology_update(topo, dtype, dst, dst_pitch, width, height, st);
+}
+
+int hrm_topology_get(hrm_topology* topo, void* stream, hrm_topology_info* out) {
+    if (!topo || !out) return fail(HRM_EINVAL, "null topology or info pointer");
+    LevelDesc d{};
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&d, topo->desc, sizeof(d), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "topology read");
+    *out = hrm_topology_info{};
+    out->dtype = topo->dtype;
+    if (topo->dtype) {
+        out->mode = d.mode;
+        out->vmin = d.vmin;
+        out->vmax = d.vmax;
+        if (d.mode == 1)  // a uniform top level leaves edge[] unused: report zeros
+            for (int i = 0; i < 17; ++i) out->edge[i] = d.edge[i];
+    }
     return HRM_OK;
 }
 

@@ -158,6 +158,15 @@ struct BatchTmp {
     double cost;
 };
 
+// A frame-stream job: its output becomes the topology's next top level.
+struct TopoUpdate {
+    hrm_topology* topo;
+    int dtype;
+    const void* dst;
+    size_t dp;
+    int W, H;
+};
+
 // Host-side plan of a batch: items in queue order plus the pre-pass list.
 template <template <class> class V>
 struct BatchPlanT {
@@ -166,6 +175,7 @@ struct BatchPlanT {
     V<LevelItem> levels;      // uniform pre-pass items
     V<int> adaptive;          // indices into levels that need the adaptive pre-pass
     V<Image> copies;          // radius-0 jobs
+    V<TopoUpdate> topos;      // frame-stream jobs, updated after the launch
     V<BatchTmp> tmp;          // planning scratch
     size_t smem = 0;
     unsigned total = 0;
@@ -184,16 +194,34 @@ static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, Batch
                  jb.dst_slice_pitch, jb.width, jb.height, jb.dims == 3 ? jb.depth : 1};
         int rc = validate(im, jb.radius, HRM_BORDER_REPLICATE, jb.flags);
         if (rc) return fail(rc, "job " + std::to_string(i) + ": " + hrm_last_error());
-        if (im.W == 0 || im.H == 0 || im.D == 0) continue;
         const long n = 2L * jb.radius + 1, N = jb.dims == 3 ? n * n * n : n * n;
         if (jb.rank < -1 || jb.rank >= N) return fail(HRM_EINVAL, "job " + std::to_string(i) + ": rank out of range");
+        const bool median = jb.rank < 0 || jb.rank == (N - 1) / 2;
+        // A frame of a stream runs as hrm_filter2d_video: the topology's top
+        // level when it holds one of this dtype, else the adaptive pre-pass.
+        unsigned flags = jb.flags;
+        const LevelDesc* given = nullptr;
+        if (jb.topo) {
+            rc = topology_check(jb.topo);
+            if (rc) return fail(rc, "job " + std::to_string(i) + ": " + hrm_last_error());
+            if (jb.dims != 2 || !median || jb.flags)
+                return fail(HRM_EINVAL, "job " + std::to_string(i) + ": a frame-stream job is a 2D median with flags 0");
+            for (const TopoUpdate& u : bp.topos)
+                if (u.topo == jb.topo)
+                    return fail(HRM_EINVAL, "job " + std::to_string(i) + ": topology already used in this batch");
+            if (im.W == 0 || im.H == 0) continue;
+            if (!bp.topos.push_back(TopoUpdate{jb.topo, jb.dtype, im.dst, im.dp, im.W, im.H}))
+                return fail(HRM_ENOTSUP, "too many jobs");
+            if (jb.topo->dtype == jb.dtype) given = jb.topo->desc;
+            else flags = HRM_ADAPTIVE;
+        }
+        if (im.W == 0 || im.H == 0 || im.D == 0) continue;
         if (jb.radius == 0) {
             if (!bp.copies.push_back(im)) return fail(HRM_ENOTSUP, "too many jobs");
             continue;
         }
-        const bool median = jb.rank < 0 || jb.rank == (N - 1) / 2;
         const uint32_t K = (uint32_t)(jb.rank < 0 ? (N + 1) / 2 : jb.rank + 1);
-        PlanH p = resolve_plan(jb.dtype, jb.dims, im.W, im.H, im.D, jb.radius, jb.flags, di, nullptr);
+        PlanH p = resolve_plan(jb.dtype, jb.dims, im.W, im.H, im.D, jb.radius, flags, di, nullptr);
         if (p.ppl != 1) {  // the persistent kernel carries only 128-output tiles (register budget)
             const size_t budget = plan_smem(p, jb.radius);
             p.ppl = 1;
@@ -238,18 +266,18 @@ static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, Batch
             h.ntiles = (int)((wtiles + BLOCK_WARPS - 1) / BLOCK_WARPS);
             t.cost = 2.0;
         } else {
-            const LevelDesc* desc = nullptr;
-            if (es == 2 || (jb.flags & HRM_ADAPTIVE)) {
+            const LevelDesc* desc = given;
+            if (!desc && (es == 2 || (flags & HRM_ADAPTIVE))) {
                 const int li = (int)bp.levels.size();
                 if (li >= dev.cap) return fail(HRM_ENOTSUP, "too many jobs for the batch buffer");
                 LevelItem L{(const unsigned char*)im.src, im.sp, im.dims == 3 ? im.sslice : 0, im.W, im.H,
-                            im.D, es, dev.descs + li, (jb.flags & HRM_ADAPTIVE) ? 1 : 0, 0};
+                            im.D, es, dev.descs + li, (flags & HRM_ADAPTIVE) ? 1 : 0, 0};
                 if (!bp.levels.push_back(L)) return fail(HRM_ENOTSUP, "too many jobs");
-                if ((jb.flags & HRM_ADAPTIVE) && !bp.adaptive.push_back(li)) return fail(HRM_ENOTSUP, "too many jobs");
+                if ((flags & HRM_ADAPTIVE) && !bp.adaptive.push_back(li)) return fail(HRM_ENOTSUP, "too many jobs");
                 desc = dev.descs + li;
             }
             t.it.kind = ITEM_HIST;
-            rc = make_hist_job(im, jb.radius, K, jb.flags, 0, p, desc, dev.err, &t.it.job);
+            rc = make_hist_job(im, jb.radius, K, flags, 0, p, desc, dev.err, &t.it.job);
             if (rc) return rc;
             bp.smem = std::max(bp.smem, plan_smem(p, jb.radius));
             // expensive tiles first: work per tile grows with the strip and the window
@@ -280,9 +308,23 @@ static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, Batch
 cudaError_t launch_levels_adaptive_only(int elem, const void* src, size_t sp, size_t slice, int W, int H,
                                         int D, LevelDesc* desc, uint32_t* hist, int num_sms, cudaStream_t st);
 
-// Enqueue a planned batch whose tables are already on the device.
+template <class Plan>
+static int enqueue_filters(const Plan& bp, const BatchDev& dev, cudaStream_t st);
+
+// Enqueue a planned batch whose tables are already on the device, then the
+// frame streams' topology updates from their outputs.
 template <class Plan>
 static int enqueue_batch(const Plan& bp, const BatchDev& dev, cudaStream_t st) {
+    int rc = enqueue_filters(bp, dev, st);
+    for (const TopoUpdate& u : bp.topos) {
+        if (rc) break;
+        rc = topology_update(u.topo, u.dtype, u.dst, u.dp, u.W, u.H, st);
+    }
+    return rc;
+}
+
+template <class Plan>
+static int enqueue_filters(const Plan& bp, const BatchDev& dev, cudaStream_t st) {
     const DeviceInfo& di = device_info();
     cudaError_t e;
     for (const Image& im : bp.copies) {
@@ -515,6 +557,12 @@ int hrm_filter_batch(const hrm_job* jobs, int njobs, void* stream) {
 int hrm_batch_graph_create(const hrm_job* jobs, int njobs, void* stream, hrm_batch_graph** out) {
     if (!out || njobs <= 0 || !jobs) return fail(HRM_EINVAL, "bad job list");
     (void)stream;
+    // the graph freezes whether a frame reads its topology or runs its own
+    // pre-pass: only the former is a frame stream on every replay
+    for (int i = 0; i < njobs; ++i)
+        if (jobs[i].topo && jobs[i].topo->dtype != jobs[i].dtype)
+            return fail(HRM_EINVAL, "job " + std::to_string(i) +
+                                        ": a graph takes a topology only once it holds a top level of the job's dtype");
     auto* g = new hrm_batch_graph();
     int rc = batchdev_alloc(g->dev, std::max(njobs, 1));
     if (rc) { delete g; return rc; }

@@ -96,4 +96,19 @@ int validate(const Image& im, int r, int border, unsigned flags);
 int make_hist_job(const Image& im, int r, uint32_t K, unsigned flags, int drop_bits, const PlanH& p,
                   const LevelDesc* desc, unsigned* err, HistJob* job);
 
+// Frame streams: the checks a frame's topology must pass (HRM_OK or
+// HRM_EINVAL with the message set), and the enqueue of its update from the
+// frame's output (records `dtype` as the descriptor's dtype on success).
+int topology_check(const hrm_topology* t);
+int topology_device_of(const hrm_topology* t);
+int topology_update(hrm_topology* t, int dtype, const void* dst, size_t dp, int W, int H, cudaStream_t st);
+
 }  // namespace hrm
+
+// Frame-stream state: the top level the next frame of the stream will use.
+struct hrm_topology {
+    int device = -1;
+    int dtype = 0;      // dtype of the frame the descriptor was made from (0: none yet)
+    hrm::LevelDesc* desc = nullptr;
+    uint32_t* hist = nullptr;
+};

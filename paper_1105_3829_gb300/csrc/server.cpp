@@ -9,6 +9,10 @@
 // and a host callback marks the wave's requests done.  Waves alternate
 // between two compute streams, so a request that arrives while earlier waves
 // are on the GPU is admitted as memory frees up and its work overlaps theirs.
+//
+// Frame streams (requests naming a topology) keep their submission order:
+// a wave holds at most one frame of each stream, and a wave that follows the
+// stream's previous frame on the other compute stream waits for that wave.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,9 +26,14 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/hrm.h"
+
+namespace hrm {
+int topology_device_of(const hrm_topology* t);  // api.cu
+}
 
 namespace {
 
@@ -102,6 +111,8 @@ struct hrm_server {
     bool stop = false;
     std::thread th;
     cudaStream_t s_copy = nullptr, s_comp[2] = {nullptr, nullptr};
+    cudaEvent_t wave_end[2] = {nullptr, nullptr};  // end of the last wave on each compute stream
+    std::unordered_map<hrm_topology*, int> topo_stream;  // compute stream of a topology's last frame
     int parity = 0;
     int inflight = 0;
     size_t resident = 0, high_water = 0;
@@ -140,12 +151,23 @@ void CUDART_CB wave_done(void* p) {
 
 // Launch every admitted request as one wave (called without the lock held).
 void launch_wave(hrm_server* s, std::vector<Req*>& batch) {
-    cudaStream_t cs = s->s_comp[s->parity];
+    const int mine = s->parity;
+    cudaStream_t cs = s->s_comp[mine];
     s->parity ^= 1;
     std::vector<hrm_job> jobs;
     jobs.reserve(batch.size());
     cudaError_t e = cudaSuccess;
     bool copied = false;
+    // a frame whose stream last ran on the other compute stream reads the
+    // topology that wave rewrites: wait for it
+    bool wait_other = false;
+    for (Req* r : batch) {
+        if (!r->q.topo) continue;
+        auto it = s->topo_stream.find(r->q.topo);
+        if (it != s->topo_stream.end() && it->second != mine) wait_other = true;
+        s->topo_stream[r->q.topo] = mine;
+    }
+    if (wait_other) e = cudaStreamWaitEvent(cs, s->wave_end[mine ^ 1], 0);
     for (Req* r : batch) {
         const hrm_request& q = r->q;
         const size_t es = elem_size(q.dtype), row = (size_t)q.width * es;
@@ -158,6 +180,7 @@ void launch_wave(hrm_server* s, std::vector<Req*>& batch) {
         j.radius = q.radius;
         j.rank = -1;
         j.flags = q.flags;
+        j.topo = q.topo;
         if (r->has_in) {
             j.src = s->arena + r->off_in;
             j.src_pitch = row;
@@ -194,6 +217,7 @@ void launch_wave(hrm_server* s, std::vector<Req*>& batch) {
         if (e != cudaSuccess) rc = HRM_ECUDA;
     }
     if (ev) cudaEventDestroy(ev);  // safe: destruction is deferred until the event completes
+    if (rc == HRM_OK && cudaEventRecord(s->wave_end[mine], cs) != cudaSuccess) rc = HRM_ECUDA;
     Wave* w = new Wave{s, batch};
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -243,8 +267,14 @@ void server_loop(hrm_server* s) {
             s->admitted.push_back(r);
         }
         if (!s->admitted.empty()) {
-            std::vector<Req*> batch;
-            batch.swap(s->admitted);
+            // one frame per stream and wave; later frames wait for the next wave
+            std::vector<Req*> batch, later;
+            std::unordered_set<hrm_topology*> frames;
+            for (Req* r : s->admitted) {
+                if (r->q.topo && !frames.insert(r->q.topo).second) later.push_back(r);
+                else batch.push_back(r);
+            }
+            s->admitted.swap(later);
             lk.unlock();
             launch_wave(s, batch);
             lk.lock();
@@ -272,7 +302,13 @@ int hrm_server_create(void* arena_dev_ptr, size_t arena_bytes, int max_inflight,
     cudaGetDevice(&s->device);
     if (cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->s_comp[0], cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&s->s_comp[1], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&s->s_comp[1], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->wave_end[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->wave_end[1], cudaEventDisableTiming) != cudaSuccess) {
+        for (cudaStream_t st : {s->s_copy, s->s_comp[0], s->s_comp[1]})
+            if (st) cudaStreamDestroy(st);
+        for (cudaEvent_t ev : s->wave_end)
+            if (ev) cudaEventDestroy(ev);
         delete s;
         return HRM_ECUDA;
     }
@@ -287,7 +323,8 @@ int hrm_submit(hrm_server* s, const hrm_request* q, uint64_t* ticket) {
     const bool bad = (q->dtype != HRM_U8 && q->dtype != HRM_U16) || q->width <= 0 || q->height <= 0 ||
                      q->radius < 0 || q->radius > HRM_MAX_RADIUS_2D || (q->flags & ~(unsigned)HRM_ADAPTIVE) ||
                      !q->src || !q->dst || q->src_pitch < (size_t)q->width * es ||
-                     q->dst_pitch < (size_t)q->width * es;
+                     q->dst_pitch < (size_t)q->width * es ||
+                     (q->topo && (q->flags || hrm::topology_device_of(q->topo) != s->device));
     std::lock_guard<std::mutex> lk(s->mu);
     if (bad || 2 * (size_t)q->width * q->height * es > s->arena_bytes) {
         s->rejected++;
@@ -379,6 +416,8 @@ int hrm_server_destroy(hrm_server* s) {
     cudaStreamDestroy(s->s_copy);
     cudaStreamDestroy(s->s_comp[0]);
     cudaStreamDestroy(s->s_comp[1]);
+    cudaEventDestroy(s->wave_end[0]);
+    cudaEventDestroy(s->wave_end[1]);
     for (auto& kv : s->live) delete kv.second;
     delete s;
     return HRM_OK;

@@ -42,7 +42,8 @@ class hrm_job(C.Structure):
     _fields_ = [("dtype", C.c_int), ("dims", C.c_int), ("src", C.c_void_p), ("src_pitch", C.c_size_t),
                 ("src_slice_pitch", C.c_size_t), ("dst", C.c_void_p), ("dst_pitch", C.c_size_t),
                 ("dst_slice_pitch", C.c_size_t), ("width", C.c_int), ("height", C.c_int),
-                ("depth", C.c_int), ("radius", C.c_int), ("rank", C.c_long), ("flags", C.c_uint)]
+                ("depth", C.c_int), ("radius", C.c_int), ("rank", C.c_long), ("flags", C.c_uint),
+                ("topo", C.c_void_p)]
 
 
 class hrm_plan(C.Structure):
@@ -54,7 +55,12 @@ class hrm_request(C.Structure):
     _fields_ = [("dtype", C.c_int), ("width", C.c_int), ("height", C.c_int), ("radius", C.c_int),
                 ("flags", C.c_uint), ("src", C.c_void_p), ("src_pitch", C.c_size_t),
                 ("dst", C.c_void_p), ("dst_pitch", C.c_size_t), ("src_on_host", C.c_int),
-                ("dst_on_host", C.c_int)]
+                ("dst_on_host", C.c_int), ("topo", C.c_void_p)]
+
+
+class hrm_topology_info(C.Structure):
+    _fields_ = [("dtype", C.c_int), ("mode", C.c_uint), ("vmin", C.c_uint), ("vmax", C.c_uint),
+                ("edge", C.c_uint * 17)]
 
 
 class hrm_server_stats(C.Structure):
@@ -77,6 +83,7 @@ SIGNATURES = {
     "hrm_topology_create": (_I, [C.POINTER(_P)]),
     "hrm_topology_destroy": (_I, [_P]),
     "hrm_filter2d_video": (_I, [_I, _P, _S, _P, _S, _I, _I, _I, _P, _P]),
+    "hrm_topology_get": (_I, [_P, _P, C.POINTER(hrm_topology_info)]),
     "hrm_filter_batch": (_I, [C.POINTER(hrm_job), _I, _P]),
     "hrm_filter_batch_noalloc": (_I, [C.POINTER(hrm_job), _I, _P]),
     "hrm_batch_graph_create": (_I, [C.POINTER(hrm_job), _I, _P, C.POINTER(_P)]),
@@ -224,8 +231,9 @@ def filter3d(vol, radius: int, adaptive: bool = False, out=None, stream=None, ra
     return out
 
 
-def make_job(src, dst, radius: int, rank: int = -1, adaptive: bool = False) -> hrm_job:
-    """Batch job descriptor for a (H, W) or (D, H, W) tensor pair."""
+def make_job(src, dst, radius: int, rank: int = -1, adaptive: bool = False, topo=None) -> hrm_job:
+    """Batch job descriptor for a (H, W) or (D, H, W) tensor pair; ``topo``
+    (a Topology) makes the job one frame of that stream."""
     es = src.element_size()
     j = hrm_job()
     j.dtype = _dtype_code(src)
@@ -239,6 +247,7 @@ def make_job(src, dst, radius: int, rank: int = -1, adaptive: bool = False) -> h
         j.depth = 1
     j.width, j.height = src.shape[-1], src.shape[-2]
     j.radius, j.rank, j.flags = radius, rank, HRM_ADAPTIVE if adaptive else 0
+    j.topo = topo._h.value if topo is not None else None
     return j
 
 
@@ -319,6 +328,12 @@ class Topology:
         check(lib().hrm_topology_create(C.byref(h)), "hrm_topology_create")
         self._h = h
 
+    def info(self, stream=None) -> dict:
+        """The top level the next frame will use (waits for ``stream``)."""
+        i = hrm_topology_info()
+        check(lib().hrm_topology_get(self._h, _stream(stream), C.byref(i)), "hrm_topology_get")
+        return {"dtype": i.dtype, "mode": i.mode, "vmin": i.vmin, "vmax": i.vmax, "edge": list(i.edge)}
+
     def close(self) -> None:
         if self._h:
             lib().hrm_topology_destroy(self._h)
@@ -354,8 +369,9 @@ class Server:
                                       max_queue, C.byref(h)), "hrm_server_create")
         self._h = h
 
-    def submit(self, src, dst, radius: int, adaptive: bool = False) -> int:
-        """Queue one 2D request; src/dst are torch tensors (CUDA or pinned CPU).
+    def submit(self, src, dst, radius: int, adaptive: bool = False, topo=None) -> int:
+        """Queue one 2D request; src/dst are torch tensors (CUDA or pinned CPU);
+        ``topo`` (a Topology) makes it the next frame of that stream.
         Returns the ticket, or raises HRMError (code HRM_EAGAIN when the queue is full)."""
         q = hrm_request()
         q.dtype = _dtype_code(src)
@@ -364,6 +380,7 @@ class Server:
         es = src.element_size()
         q.src, q.src_pitch, q.src_on_host = src.data_ptr(), src.stride(0) * es, int(not src.is_cuda)
         q.dst, q.dst_pitch, q.dst_on_host = dst.data_ptr(), dst.stride(0) * es, int(not dst.is_cuda)
+        q.topo = topo._h.value if topo is not None else None
         t = C.c_uint64()
         rc = lib().hrm_submit(self._h, C.byref(q), C.byref(t))
         if rc != HRM_OK:

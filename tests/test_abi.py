@@ -41,9 +41,38 @@ def test_binding_covers_the_header():
     assert set(declared_functions()) <= set(hrm.SIGNATURES)
 
 
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structures have the sizes and field offsets the C compiler
+    gives the header's structs (a field added on one side only fails here)."""
+    import shutil
+    import subprocess
+    from paper_1105_3829_gb300 import hrm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [hrm.hrm_job, hrm.hrm_request, hrm.hrm_plan, hrm.hrm_server_stats, hrm.hrm_topology_info]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hrm.h"', "int main(void) {"]
+    for st in structs:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (st.__name__, st.__name__))
+        for f in st._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));'
+                         % (st.__name__, f[0], st.__name__, f[0]))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                 text=True).stdout.splitlines())
+    for st in structs:
+        assert int(got[st.__name__]) == ctypes.sizeof(st), st.__name__
+        for f in st._fields_:
+            assert int(got[st.__name__ + "." + f[0]]) == getattr(st, f[0]).offset, (st.__name__, f[0])
+
+
 def test_version_and_error_string(lib):
     from paper_1105_3829_gb300 import hrm
-    assert hrm.hrm_version() == 100
+    assert hrm.hrm_version() == 110
     assert isinstance(hrm.last_error(), str)
 
 
