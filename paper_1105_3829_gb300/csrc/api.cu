@@ -82,7 +82,7 @@ int workspace_for(cudaStream_t st, Workspace** out) {
     w.err = (unsigned*)p;
     p += 256;
     w.counters = (unsigned*)p;
-    e = cudaMemset(base, 0, bytes);
+    e = cudaMemsetAsync(base, 0, bytes, st);  // ordered with the stream's own work
     if (e != cudaSuccess) return cuda_fail(e, "workspace memset");
     *out = &(g_ws[key] = w);
     return HRM_OK;

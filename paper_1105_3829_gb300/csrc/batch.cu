@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <type_traits>
@@ -94,7 +95,10 @@ struct BatchDev {
     int stage_next = 0;
 };
 
-static int batchdev_alloc(BatchDev& b, int cap) {
+// The buffer is cleared on `st`, the stream its tables are uploaded and used
+// on (a plain cudaMemset would run on the legacy default stream, which does
+// not order against non-blocking streams).
+static int batchdev_alloc(BatchDev& b, int cap, cudaStream_t st) {
     const size_t bytes = sizeof(BatchItem) * cap + sizeof(unsigned) * (cap + 1) + sizeof(LevelItem) * cap +
                          sizeof(LevelDesc) * cap + 256 + sizeof(uint32_t) * 2 * 4096 + 256;
     void* p = nullptr;
@@ -111,7 +115,7 @@ static int batchdev_alloc(BatchDev& b, int cap) {
     align(q); b.counter = (unsigned*)q; q += 128;
     b.err = (unsigned*)q; q += 128;
     align(q); b.hist = (uint32_t*)q;
-    e = cudaMemset(p, 0, bytes);
+    e = cudaMemsetAsync(p, 0, bytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch buffer memset");
     return HRM_OK;
 }
@@ -415,29 +419,33 @@ static int upload_plan(const BatchPlan& bp, BatchDev& dev, cudaStream_t st, bool
     return e == cudaSuccess ? HRM_OK : cuda_fail(e, "batch table upload");
 }
 
-// Per-(device, stream) batch buffers for hrm_filter_batch.
+// Per-(device, stream) batch buffers for hrm_filter_batch (a map: the
+// returned reference stays valid while other streams add entries).
 static std::mutex g_bmu;
-static std::vector<std::pair<std::pair<int, cudaStream_t>, BatchDev>> g_bufs;
+static std::map<std::pair<int, cudaStream_t>, BatchDev> g_bufs;
 
 static int batch_buffers(cudaStream_t st, int need, BatchDev** out) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_bmu);
-    for (auto& kv : g_bufs)
-        if (kv.first.first == dev && kv.first.second == st) {
-            if (kv.second.cap < need) {
-                cudaStreamSynchronize(st);  // the old tables may still be in use
-                batchdev_free(kv.second);
-                int rc = batchdev_alloc(kv.second, std::max(need, 256));
-                if (rc) return rc;
-            }
-            *out = &kv.second;
-            return HRM_OK;
+    auto it = g_bufs.find({dev, st});
+    if (it != g_bufs.end()) {
+        if (it->second.cap < need) {
+            cudaStreamSynchronize(st);  // the old tables may still be in use
+            batchdev_free(it->second);
+            int rc = batchdev_alloc(it->second, std::max(need, 256), st);
+            if (rc) return rc;
         }
-    g_bufs.push_back({{dev, st}, BatchDev{}});
-    int rc = batchdev_alloc(g_bufs.back().second, std::max(need, 256));
-    if (rc) return rc;
-    *out = &g_bufs.back().second;
+        *out = &it->second;
+        return HRM_OK;
+    }
+    BatchDev& b = g_bufs[{dev, st}];
+    int rc = batchdev_alloc(b, std::max(need, 256), st);
+    if (rc) {
+        g_bufs.erase({dev, st});
+        return rc;
+    }
+    *out = &b;
     return HRM_OK;
 }
 
@@ -564,7 +572,7 @@ int hrm_batch_graph_create(const hrm_job* jobs, int njobs, void* stream, hrm_bat
             return fail(HRM_EINVAL, "job " + std::to_string(i) +
                                         ": a graph takes a topology only once it holds a top level of the job's dtype");
     auto* g = new hrm_batch_graph();
-    int rc = batchdev_alloc(g->dev, std::max(njobs, 1));
+    int rc = batchdev_alloc(g->dev, std::max(njobs, 1), nullptr);  // the table upload below is synchronous
     if (rc) { delete g; return rc; }
     rc = plan_batch(jobs, njobs, g->dev, g->plan);
     if (!rc) rc = upload_plan(g->plan, g->dev, nullptr, true);

@@ -158,9 +158,13 @@ __global__ void __launch_bounds__(1024) edges_kernel(LevelDesc* d, const uint32_
     const uint64_t av = (uint64_t)vmin + (uint64_t)a * binw;
     uint64_t bv = (uint64_t)vmin + (uint64_t)(b + 1) * binw - 1;
     if (bv > vmax) bv = vmax;
+    if (bv < av) {  // cannot happen for a histogram of values in [vmin, vmax]; keep the uniform tree
+        d->mode = 0;
+        return;
+    }
     // smallest w = 16^k with 13 w >= the central range (one interval of slack for the alignment)
     uint64_t w = 16;
-    while (13 * w < bv - av + 1) w <<= 4;
+    while (w < (1ull << 32) && 13 * w < bv - av + 1) w <<= 4;
     if (ushift <= 0 || w >= (1ull << ushift)) {  // not finer than the uniform tree
         d->mode = 0;
         return;
