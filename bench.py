@@ -364,10 +364,53 @@ def run_video(args, hrm, inputs, torch, dev, flush):
             row[mode] = {"ms_per_frame": float(np.mean(times)), "mpix_s": out.numel() / float(np.mean(times)) / 1e3}
         res["r%d" % r] = row
     value = float(np.mean([res[k]["video"]["mpix_s"] for k in res]))
+    res["served"] = _served_streams(hrm, inputs, torch, dev)
     _line("frame stream: output Mpix/s with the previous frame's topology (mean over r=15,50)", "Mpix/s", value,
           {"dtype": "u16", "cases": res, "config": {"workload": "video: 8 frames 4096^2 uint16 low-key, blobs "
-                                                    "drifting 4 px/frame", "l2": "flushed before every timed call"}},
+                                                    "drifting 4 px/frame; served: 4 streams x 8 frames 2048^2 "
+                                                    "through the server", "l2": "flushed before every timed call "
+                                                    "(served: host wall clock, submit of the first frame to the "
+                                                    "poll of the last)"}},
           args)
+
+
+def _served_streams(hrm, inputs, torch, dev, nstreams=4, nframes=8, side=2048, r=15):
+    """Several frame streams through the serving loop, all frames submitted
+    at once: each stream keeps its order (one frame per wave) while frames of
+    different streams share waves.  Wall-clock throughput with a topology per
+    stream vs the same frames as plain requests (uniform tree)."""
+    import time
+    streams = [[torch.from_numpy(f).to(dev) for f in inputs.video_frames(nframes, side, side, drift=4,
+                                                                          seed=inputs.seed_for(6, 10 + k))]
+               for k in range(nstreams)]
+    outs = [[torch.empty_like(f) for f in s] for s in streams]
+    arena = torch.empty(4 << 30, dtype=torch.uint8, device=dev)
+    row = {}
+    for mode in ("plain", "topology"):
+        best = waves = None
+        for rep in range(2):  # the first pass warms up plans and topologies
+            srv = hrm.Server(arena, max_inflight=4096, max_queue=16384)
+            topos = [hrm.Topology() for _ in range(nstreams)] if mode == "topology" else [None] * nstreams
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tickets = [srv.submit(streams[k][f], outs[k][f], r, topo=topos[k])
+                       for f in range(nframes) for k in range(nstreams)]
+            for i, t in enumerate(tickets):
+                rc = srv.poll(t, 60_000_000)  # bounded: a lost wave fails the run instead of hanging it
+                if rc != hrm.HRM_OK:
+                    raise RuntimeError("served frame %d (%s) failed: %d" % (i, mode, rc))
+            dt = time.perf_counter() - t0
+            waves = int(srv.stats().waves)
+            srv.close()
+            for t in topos:
+                if t is not None:
+                    t.close()
+            if rep:
+                best = dt
+        npx = nstreams * nframes * side * side
+        row[mode] = {"wall_ms": best * 1e3, "mpix_s": npx / best / 1e6, "waves": waves}
+    row["config"] = "%d streams x %d frames %d^2 uint16 low-key, r=%d" % (nstreams, nframes, side, r)
+    return row
 
 
 def run_paper(args, hrm, inputs, torch, dev, flush):

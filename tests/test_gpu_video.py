@@ -182,3 +182,30 @@ def test_server_frame_streams_keep_order(hrm, oracle):
     _same_top_level(tb, vb)
     for t in (ta, tb, va, vb):
         t.close()
+
+
+def test_server_large_frames_first_waves(hrm):
+    """A fresh server whose first wave runs long (whole 2048^2 low-key
+    frames) while its next wave starts on the other, still unused compute
+    stream: the new stream's buffers must be cleared in that stream's order,
+    not on the legacy default stream behind the running kernel."""
+    from paper_1105_3829_gb300 import inputs
+    fr = [torch.from_numpy(x).cuda() for x in inputs.video_frames(4, 2048, 2048, drift=4, seed=91)]
+    arena = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    for with_topo in (False, True):
+        srv = hrm.Server(arena, max_inflight=4096, max_queue=16384)
+        topos = [hrm.Topology() if with_topo else None for _ in range(4)]
+        outs = [[torch.empty_like(fr[0]) for _ in range(2)] for _ in range(4)]
+        try:
+            tickets = [srv.submit(fr[(k + f) % 4], outs[k][f], 15, topo=topos[k]) for f in range(2) for k in range(4)]
+            assert [srv.poll(t, 60_000_000) for t in tickets] == [hrm.HRM_OK] * len(tickets)
+        finally:
+            srv.close()
+        for k in range(4):
+            for f in range(2):
+                want = hrm.filter2d(fr[(k + f) % 4], 15)
+                torch.cuda.synchronize()
+                assert torch.equal(outs[k][f].view(torch.int16), want.view(torch.int16)), (with_topo, k, f)
+        for t in topos:
+            if t is not None:
+                t.close()
