@@ -237,7 +237,18 @@ int hrm_batch_graph_destroy(hrm_batch_graph* g);
  * plan file before the first call (a missing or malformed file is ignored);
  * HRM_FORCE_PATH=hist or =sortnet forces the histogram kernel or the
  * selection networks (where one exists for the problem) in every call
- * without an explicit plan.  Outputs never depend on the plan. */
+ * without an explicit plan.  Outputs never depend on the plan.
+ *
+ * Node-cache feedback (2D single-image calls of a class with no set, tuned
+ * or forced plan): the first call counts how many tree nodes its tiles had to
+ * build and copies the count back asynchronously; once that copy has landed
+ * (a non-blocking check at a later call of the class), a class whose tile rows
+ * built more than 0.75 nodes on average tries as many cached nodes as fit in
+ * up to 200 KB per tile (one or two tiles per SM) instead of the default four
+ * tiles per SM; that trial call is counted too, and the class keeps the large
+ * cache only if it cut the node builds at least 3-fold.  Nothing waits for
+ * the counts.  hrm_get_plan reports the plan a single call of the class
+ * would use now, feedback included. */
 typedef struct {
     int tile_width;     /* output columns per tile: 128 or 256 (0 = default) */
     int strip_height;   /* output rows (2D) or slices (3D) per tile (0 = default) */

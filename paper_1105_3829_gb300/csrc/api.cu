@@ -228,14 +228,135 @@ static void apply_plan(PlanH& p, const hrm_plan& hp, int dims, int W, int lines,
     if (hp.path == 1 || hp.path == 2) p.path = hp.path;
 }
 
+// ---- node-cache feedback (2D histogram kernel, default plans only) ----------------
+// The default plan (four tiles of ~55 KB per SM) suits images whose tile rows
+// reuse a few tree nodes.  Rows that visit a few dozen distinct nodes (noisy
+// 16-bit images with a compact mode) rebuild nodes all the time and run 2-3x
+// faster with as many node slots as fit in up to 200 KB per tile (one or two
+// tiles per SM); rows that visit even more (wide 16-bit distributions) rebuild
+// with either cache and lose by the fewer warps.  Which case a problem class
+// is cannot be seen on the host without reading the image, so the class is
+// measured: its first call counts the node installs of its tiles into a
+// device counter and copies the count back asynchronously.  A later call
+// checks the copy with a non-blocking event query; if a tile row installed
+// more than FB_DEEP_RATE nodes, the next call runs the large-cache plan and is
+// counted the same way, and the class keeps that plan only if it cut the
+// installs at least FB_KEEP_CUT-fold, else it returns to the default for good.
+// Nothing waits, and outputs never depend on the plan.  A set, tuned or
+// forced plan takes precedence and switches the feedback off for its class.
+constexpr int FB_MAX = 4096;             // counters per device
+constexpr double FB_DEEP_RATE = 0.75;    // node installs per tile row that call for a trial
+constexpr double FB_KEEP_CUT = 3.0;      // the trial must cut the installs this much
+constexpr int FB_DEEP_KBYTES = 200;      // shared-memory budget per tile of the large-cache plan
+struct FbDevice {
+    unsigned* d = nullptr;  // FB_MAX device counters
+    unsigned* h = nullptr;  // their pinned copies
+    int used = 0;
+};
+// States: 0 unmeasured; 1 default count in flight; 2 decided (deep or not);
+// 3 trial of the large cache due; 4 trial count in flight.
+struct FbClass {
+    int state = 0;
+    int idx = -1;
+    double rows = 0;        // tile rows of a counted launch
+    double rate0 = 0;       // installs per tile row with the default plan
+    cudaEvent_t ev = nullptr;
+    bool deep = false;
+};
+static std::map<int, FbDevice> g_fbdev;
+static std::map<std::pair<int, std::tuple<int, int, int, int, int, int, unsigned>>, FbClass> g_fb;
+
+static bool fb_eligible(const ProblemKey& k, const hrm_plan* force) {
+    hrm_plan hp;
+    return k.dims == 2 && !force && !env_forced_path() && !plan_lookup(k, &hp);
+}
+
+// Should this call of the class run the large-cache plan?  (Never blocks.)
+static bool fb_deep(const ProblemKey& k) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_fb.find({dev, tkey(k)});
+    if (it == g_fb.end()) return false;
+    FbClass& c = it->second;
+    if (c.state == 1 || c.state == 4) {
+        const bool clean = cudaPeekAtLastError() == cudaSuccess;
+        const cudaError_t q = cudaEventQuery(c.ev);
+        if (q == cudaSuccess) {
+            const double rate = c.rows > 0 ? (double)g_fbdev[dev].h[c.idx] / c.rows : 0.0;
+            if (c.state == 1) {
+                c.rate0 = rate;
+                c.state = rate > FB_DEEP_RATE ? 3 : 2;
+                c.deep = false;
+            } else {
+                c.deep = rate * FB_KEEP_CUT <= c.rate0;
+                c.state = 2;
+            }
+        } else if (clean) {
+            cudaGetLastError();  // a not-ready answer is not an error of a later call
+        }
+    }
+    return c.state == 3 || c.state == 4 || (c.state == 2 && c.deep);
+}
+
+// A counted launch is due (first call, or the trial of the large cache): a
+// zeroed device counter for it, else null.
+static unsigned* fb_begin(const ProblemKey& k, double rows, cudaStream_t st) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    FbClass& c = g_fb[{dev, tkey(k)}];
+    if (c.state != 0 && c.state != 3) return nullptr;
+    const int next = c.state == 0 ? 1 : 4;
+    c.state = 2;  // unless everything below succeeds, the class keeps the default plan
+    c.deep = false;
+    FbDevice& fd = g_fbdev[dev];
+    if (!fd.d) {
+        if (cudaMalloc(&fd.d, sizeof(unsigned) * FB_MAX) != cudaSuccess) return (void)cudaGetLastError(), nullptr;
+        if (cudaMallocHost(&fd.h, sizeof(unsigned) * FB_MAX) != cudaSuccess) return (void)cudaGetLastError(), nullptr;
+        memset(fd.h, 0, sizeof(unsigned) * FB_MAX);
+    }
+    if (!fd.h) return nullptr;
+    if (c.idx < 0) {
+        if (fd.used >= FB_MAX) return nullptr;
+        if (cudaEventCreateWithFlags(&c.ev, cudaEventDisableTiming) != cudaSuccess)
+            return (void)cudaGetLastError(), nullptr;
+        c.idx = fd.used++;
+    }
+    c.rows = rows;
+    if (cudaMemsetAsync(fd.d + c.idx, 0, sizeof(unsigned), st) != cudaSuccess) return (void)cudaGetLastError(), nullptr;
+    c.state = next;
+    return fd.d + c.idx;
+}
+
+// After a counted launch: bring the count back and mark when it lands.
+static void fb_end(const ProblemKey& k, cudaStream_t st) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    FbClass& c = g_fb[{dev, tkey(k)}];
+    FbDevice& fd = g_fbdev[dev];
+    if (cudaMemcpyAsync(fd.h + c.idx, fd.d + c.idx, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaEventRecord(c.ev, st) != cudaSuccess) {
+        cudaGetLastError();
+        c.state = 2;
+        c.deep = false;
+    }
+}
+
 PlanH resolve_plan(int dtype, int dims, int W, int H, int D, int r, unsigned flags, const DeviceInfo& di,
-                   const hrm_plan* force) {
+                   const hrm_plan* force, bool feedback) {
     const int lines = dims == 3 ? H : 1;
     const int walk = dims == 3 ? D : H;
     const int es = dtype == HRM_U16 ? 2 : 1;
     PlanH p = default_plan(dims, es, W, lines, walk, r, di);
     hrm_plan hp;
-    if (plan_lookup(ProblemKey{dtype, dims, W, H, D, r, flags}, &hp)) apply_plan(p, hp, dims, W, lines, walk, r, di);
+    const ProblemKey key{dtype, dims, W, H, D, r, flags};
+    if (plan_lookup(key, &hp)) apply_plan(p, hp, dims, W, lines, walk, r, di);
+    else if (feedback && p.path == 2 && fb_eligible(key, force) && fb_deep(key)) {
+        const hrm_plan deep{0, p.sh, FB_DEEP_KBYTES, 0};  // one tile per SM, the default strips
+        apply_plan(p, deep, dims, W, lines, walk, r, di);
+    }
     if (force) apply_plan(p, *force, dims, W, lines, walk, r, di);
     else if (env_forced_path()) p.path = env_forced_path();
     // the shared-memory plan must fit the device
@@ -340,7 +461,7 @@ int filter_impl(const Image& im, int r, long rank, unsigned flags, int drop_bits
     const uint32_t K = (uint32_t)(rank < 0 ? (N + 1) / 2 : rank + 1);
     if (r == 0) return copy_image(im, st);
     const DeviceInfo& di = device_info();
-    const PlanH p = resolve_plan(im.dtype, im.dims, im.W, im.H, im.D, r, flags, di, force);
+    const PlanH p = resolve_plan(im.dtype, im.dims, im.W, im.H, im.D, r, flags, di, force, true);
     cudaError_t e;
     if (im.dims == 2 && p.path == 1 && r <= SORTNET_MAX_R2D && median && drop_bits == 0) {
         // rows per warp: about 32 warp tiles per SM (latency hiding for the
@@ -373,8 +494,15 @@ int filter_impl(const Image& im, int r, long rank, unsigned flags, int drop_bits
     if (rc) return rc;
     if (plan_smem(p, r) > (size_t)di.smem_optin)
         return fail(HRM_ENOTSUP, "plan needs more shared memory than the device offers");
+    const ProblemKey key{im.dtype, im.dims, im.W, im.H, im.D, r, flags};
+    if (p.path == 2 && drop_bits == 0 && fb_eligible(key, force)) {
+        const double rows = (double)((im.W + BLOCK_THREADS * p.ppl - 1) / (BLOCK_THREADS * p.ppl)) * im.H;
+        job.stats = fb_begin(key, rows, st);
+    }
     e = launch_hist(job, st);
-    return e == cudaSuccess ? HRM_OK : cuda_fail(e, "hist launch");
+    if (e != cudaSuccess) return cuda_fail(e, "hist launch");
+    if (job.stats) fb_end(key, st);
+    return HRM_OK;
 }
 
 int topology_check(const hrm_topology* t) {
@@ -539,7 +667,7 @@ int hrm_get_plan(int dtype, int dims, int width, int height, int depth, int radi
     ProblemKey k{dtype, dims, width, height, depth, radius, flags};
     if (plan_lookup(k, plan)) return HRM_OK;
     const DeviceInfo& di = device_info();
-    PlanH p = resolve_plan(dtype, dims, width, height, depth, radius, flags, di, nullptr);
+    PlanH p = resolve_plan(dtype, dims, width, height, depth, radius, flags, di, nullptr, true);
     plan->tile_width = BLOCK_THREADS * p.ppl;
     plan->strip_height = p.sh;
     plan->slot_kbytes = (int)((plan_smem(p, radius) + 1023) / 1024);

@@ -117,7 +117,8 @@ struct Meta {
     uint32_t preq[PREQ_SIZE];   // pending requests of this round (keys)
     uint32_t req[REQ_MAX];      // distinct requested keys in arrival order
     uint32_t nbuild;
-    uint32_t pad2[3];
+    uint32_t ninst;             // build entries installed by this tile (node-cache feedback)
+    uint32_t pad2[2];
     uint32_t build_slot[MAX_SLOTS];
     uint32_t build_key[MAX_SLOTS];
     uint32_t wtot[8][8];        // per-warp totals of the block prefix scan

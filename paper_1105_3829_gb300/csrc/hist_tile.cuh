@@ -72,6 +72,7 @@ struct HistJob {
     int cw;                  // counter width in bytes (1 or 2)
     int ring;                // 2D only: stage the last n+1 input rows in shared memory
     unsigned* err;           // device error word (may be null)
+    unsigned* stats;         // null, or a counter that receives the tiles' node installs
 };
 
 // Ring of the last n+1 input rows (2D): (n+1) rows x NC columns, padded to 16 bytes.
@@ -521,6 +522,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     if (warp == 0) {
         load_levels(m, a.desc, a.fixed_shift);
         slots_reset(m);
+        if (lane == 0) m.ninst = 0;
     }
     if (use_ring) {  // stage input rows ts-r-1 .. ts+r
         for (int u = ts - r - 1; u <= ts + r; ++u) {
@@ -812,6 +814,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                         }
                         if (lane == 0) {
                             m.nbuild = nb;
+                            m.ninst += nb;
                             m.build_off[nb] = off;
                         }
                     }
@@ -938,6 +941,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     if (tid == 0) {
         oc.flush(tile);
         oc.tile(tile, ns_tile0);
+        if (a.stats) atomicAdd(a.stats, m.ninst);  // thread 0 is the only writer of m.ninst
     }
 }
 

@@ -61,8 +61,10 @@ int strip_layout(int walk, int sh, int r, int* she, int* ne);
 void size_slots(PlanH& p, int dims, int r, size_t budget);
 int strip_length(int dims, int W, int lines, int walk, int r, int tw, size_t smem, const DeviceInfo& di);
 PlanH default_plan(int dims, int es, int W, int lines, int walk, int r, const DeviceInfo& di);
+// feedback: single-image 2D calls may switch an unplanned class to the
+// large-node-cache plan after its first call measured many node installs.
 PlanH resolve_plan(int dtype, int dims, int W, int H, int D, int r, unsigned flags, const DeviceInfo& di,
-                   const hrm_plan* force);
+                   const hrm_plan* force, bool feedback = false);
 int slots_for(int tw, int r, int cw, size_t budget);
 size_t plan_smem(const PlanH& p, int r);
 int counter_width(int dims, int r);

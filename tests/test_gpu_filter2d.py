@@ -260,3 +260,31 @@ def test_very_large_image_sampled(hrm, oracle):
         got = got.cpu().numpy().view(np.uint16)  # (CUDA indexing has no uint16 kernel)
         np.testing.assert_array_equal(got, oracle.points(img, r, ys, xs))
         del out
+
+
+def test_node_cache_feedback(hrm, oracle):
+    """A noisy 16-bit image with a compact mode (a few dozen distinct nodes
+    per tile row) moves its class to the large node cache: the first call
+    reports many node installs, the second (the large-cache trial) far fewer.
+    An x-ray image keeps the default plan.  Every call is exact."""
+    from paper_1105_3829_gb300 import inputs
+    cases = [("lowkey", inputs.lowkey16_u16(301, 517, seed=61), True),
+             ("xray", inputs.xray12_u16(299, 515, seed=62), False)]
+    for name, img, deep in cases:
+        h, w = img.shape
+        src = torch.from_numpy(img).cuda()
+        before = hrm.get_plan(hrm.HRM_U16, 2, w, h, 1, 15)
+        want = oracle.median2d(img, 15)
+        for call in range(3):
+            got = hrm.filter2d(src, 15)
+            hrm.device_status()
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(got.cpu().numpy(), want, err_msg="%s call %d" % (name, call))
+        after = hrm.get_plan(hrm.HRM_U16, 2, w, h, 1, 15)
+        assert before.slot_kbytes < 100, (name, before.slot_kbytes)
+        if deep:
+            # as many node slots as fit in up to 200 KB (the slot count caps it): one or two tiles per SM
+            assert after.slot_kbytes >= before.slot_kbytes + 30 and after.strip_height == before.strip_height, \
+                (name, before.slot_kbytes, after.slot_kbytes)
+        else:
+            assert after.slot_kbytes == before.slot_kbytes, (name, after.slot_kbytes)
