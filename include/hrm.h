@@ -280,7 +280,9 @@ int hrm_plan_load(const char* path);
  * order, each with the top level left by the one before it; two frames of one
  * stream never share a wave (the later one waits for the next), and a wave
  * on the other compute stream waits for the wave that last used the
- * topology.  The topology must outlive its requests. */
+ * topology.  The topology must outlive its requests, and while the server
+ * holds requests for it no other call may use it (the server's streams are
+ * not ordered with the caller's). */
 typedef struct hrm_server hrm_server;
 
 typedef struct {
