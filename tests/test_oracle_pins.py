@@ -180,6 +180,15 @@ def test_rank_matches_scipy_rank_filter(oracle, rank):
     np.testing.assert_array_equal(oracle.median2d(img, 2, rank=rank), exp)
 
 
+@pytest.mark.parametrize("rank", [0, 13, 26])
+def test_rank_3d_matches_scipy_rank_filter(oracle, rank):
+    """Order statistics over the cubic 3x3x3 window (minimum, median, maximum)
+    against the library routine, replicate border."""
+    vol = _rand((7, 9, 10), np.uint8, 83, hi=256)
+    exp = scipy_ndimage.rank_filter(vol, rank, size=3, mode="nearest")
+    np.testing.assert_array_equal(oracle.median3d(vol, 1, rank=rank), exp)
+
+
 # ---- internal consistency ---------------------------------------------------
 
 def test_sort_select_numpy_and_points_agree(oracle):
