@@ -145,3 +145,36 @@ def test_environment_plan_cache_and_forced_path(lib, tmp_path):
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
     assert out.returncode == 0, out.stderr[-2000:]
     assert out.stdout.split()[3:] == ["1", "1"]
+
+
+def test_server_topology_and_graph_arguments_without_device(lib):
+    """Null handles and malformed arguments are refused on the host, before
+    any device work: serving, frame-stream topologies, graphs, plans."""
+    from paper_1105_3829_gb300 import hrm
+    E = hrm.HRM_EINVAL
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(1 << 12)
+    arena = ctypes.addressof(buf)
+    assert hrm.hrm_server_create(None, 1 << 20, 8, 0, ctypes.byref(h)) == E       # no arena
+    assert hrm.hrm_server_create(arena, 0, 8, 0, ctypes.byref(h)) == E             # empty arena
+    assert hrm.hrm_server_create(arena, 1 << 12, 0, 0, ctypes.byref(h)) == E       # no in-flight slots
+    assert hrm.hrm_server_create(arena, 1 << 12, 8, -1, ctypes.byref(h)) == E      # negative queue
+    t = ctypes.c_uint64()
+    assert hrm.hrm_submit(None, None, ctypes.byref(t)) == E
+    assert hrm.hrm_poll(None, 1, 0) == E
+    assert hrm.hrm_ticket_latency_us(None, 1) < 0
+    assert hrm.hrm_server_stats_get(None, None) == E
+    assert hrm.hrm_server_destroy(None) == hrm.HRM_OK
+    info = hrm.hrm_topology_info()
+    assert hrm.hrm_topology_get(None, None, ctypes.byref(info)) == E
+    assert hrm.hrm_topology_destroy(None) == hrm.HRM_OK
+    assert hrm.hrm_topology_create(None) == E
+    g = ctypes.c_void_p()
+    jobs = (hrm.hrm_job * 1)()
+    assert hrm.hrm_batch_graph_create(jobs, 0, None, ctypes.byref(g)) == E
+    assert hrm.hrm_batch_graph_create(None, 1, None, ctypes.byref(g)) == E
+    assert hrm.hrm_batch_graph_launch(None, None) == E
+    p = hrm.hrm_plan()
+    assert hrm.hrm_get_plan(2, 4, 64, 64, 1, 5, 0, ctypes.byref(p)) == E           # dims
+    assert hrm.hrm_set_plan(2, 2, 64, 64, 1, 5, 0, ctypes.byref(hrm.hrm_plan(64, 0, 0, 0))) == E   # tile width
+    assert hrm.hrm_set_plan(2, 2, 64, 64, 1, 5, 0, ctypes.byref(hrm.hrm_plan(0, 0, 0, 3))) == E    # path
