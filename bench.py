@@ -252,11 +252,18 @@ def _timed(fn, flush, reps=5, warm=2):
     return np.array(out)
 
 
-def _line(metric, unit, value, extra, args, hib=True):
+def _line(metric, unit, value, extra, args, hib=True, clk=None):
     d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
          "higher_is_better": hib, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
     d.update(extra)
+    if clk is not None:
+        d["clocks"] = clk.summary()
     print(json.dumps(d))
+
+
+def _smi_index(local: int = 0) -> str:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    return vis.split(",")[local].strip() if vis else str(local)
 
 
 def run_secondary(args):
@@ -273,6 +280,7 @@ def run_secondary(args):
         octs = [torch.from_numpy(o).to(dev) for o in inputs.octants(vol_np)]
         nvox = vol.numel()
         res = {}
+        clk = ClockSampler(_smi_index()).__enter__()
         for r in (1, 3, 7):
             out = torch.empty_like(vol)
             outs = [torch.empty_like(o) for o in octs]
@@ -291,12 +299,13 @@ def run_secondary(args):
                            "p50_ms": {"single": med(t_single), "batch": med(t_batch), "graph": med(t_graph),
                                       "separate": med(t_sep)},
                            "p99_ms_batch": float(np.percentile(t_batch, 99))}
+        clk.__exit__()
         value = float(np.mean([v["octants_one_launch_mvox_s"] for v in res.values()]))
         _line("3D median, uint16 256^3 as 8 x 128^3 in one launch: output Mvox/s (mean over r=1,3,7)", "Mvox/s",
               value, {"dtype": "u16", "per_radius": res,
                       "config": {"workload": "3D median 256^3 uint16 x-ray mixture + 3D low-frequency noise; "
                                              "8 octant volumes in one persistent launch vs one 256^3 volume vs 8 "
-                                             "launches", "l2": "flushed before every timed call"}}, args)
+                                             "launches", "l2": "flushed before every timed call"}}, args, clk=clk)
     elif args.workload in ("lowkey2d", "u8small"):
         if args.workload == "lowkey2d":
             img_np, radii, dt = inputs.lowkey16_u16(), (15, 50), "u16"
@@ -305,6 +314,7 @@ def run_secondary(args):
         img = torch.from_numpy(img_np).to(dev)
         out = torch.empty_like(img)
         res = {}
+        clk = ClockSampler(_smi_index()).__enter__()
         for r in radii:
             for ad in ((False, True) if args.workload == "lowkey2d" else (False,)):
                 t = _timed(lambda: hrm.filter2d(img, r, adaptive=ad, out=out), flush, reps)
@@ -318,12 +328,14 @@ def run_secondary(args):
                                          "plan": {"tile_width": plan.tile_width, "strip_height": plan.strip_height,
                                                   "slot_kbytes": plan.slot_kbytes, "path": plan.path}}
                 res["r%d%s" % (r, "_adaptive" if ad else "")] = case
+        clk.__exit__()
         value = float(np.mean([v.get("autotuned", v)["mpix_s"] for v in res.values()]))
         _line("2D median %s: output Mpix/s (mean over cases%s)" % ("8192^2 uint16 low-key" if dt == "u16" else
                                                                "512^2 uint8 uniform r=3",
                                                                ", autotuned plans" if dt == "u16" else ""),
               "Mpix/s", value, {"dtype": dt, "cases": res,
-                                "config": {"workload": args.workload, "l2": "flushed before every timed call"}}, args)
+                                "config": {"workload": args.workload, "l2": "flushed before every timed call"}}, args,
+              clk=clk)
     elif args.workload == "video":
         run_video(args, hrm, inputs, torch, dev, flush)
     elif args.workload == "paper":
@@ -341,6 +353,7 @@ def run_video(args, hrm, inputs, torch, dev, flush):
     frames = [torch.from_numpy(f).to(dev) for f in inputs.video_frames(8, 4096, 4096, drift=4)]
     out = torch.empty_like(frames[0])
     res = {}
+    clk = ClockSampler(_smi_index()).__enter__()
     for r in (15, 50):
         row = {}
         for mode in ("uniform", "adaptive", "video"):
@@ -365,13 +378,14 @@ def run_video(args, hrm, inputs, torch, dev, flush):
         res["r%d" % r] = row
     value = float(np.mean([res[k]["video"]["mpix_s"] for k in res]))
     res["served"] = _served_streams(hrm, inputs, torch, dev)
+    clk.__exit__()
     _line("frame stream: output Mpix/s with the previous frame's topology (mean over r=15,50)", "Mpix/s", value,
           {"dtype": "u16", "cases": res, "config": {"workload": "video: 8 frames 4096^2 uint16 low-key, blobs "
                                                     "drifting 4 px/frame; served: 4 streams x 8 frames 2048^2 "
                                                     "through the server", "l2": "flushed before every timed call "
                                                     "(served: host wall clock, submit of the first frame to the "
                                                     "poll of the last)"}},
-          args)
+          args, clk=clk)
 
 
 def _served_streams(hrm, inputs, torch, dev, nstreams=4, nframes=8, side=2048, r=15):
@@ -424,6 +438,7 @@ def run_paper(args, hrm, inputs, torch, dev, flush):
              "normal16": inputs.paper_normal(4096, 4096, 16, seed=inputs.seed_for(7, 2)),
              "sine100_16": inputs.paper_sine(4096, 4096, 100, 16)}
     res = {}
+    clk = ClockSampler(_smi_index()).__enter__()
     for name, a in cases.items():
         img = torch.from_numpy(a).to(dev)
         out = torch.empty_like(img)
@@ -431,21 +446,24 @@ def run_paper(args, hrm, inputs, torch, dev, flush):
             t = _timed(lambda: hrm.filter2d(img, 25, adaptive=ad, out=out), flush, max(3, args.steps))
             ms = float(np.median(t))
             res["%s%s" % (name, "_adaptive" if ad else "")] = {"p50_ms": ms, "mpix_s": img.numel() / ms / 1e3}
+    clk.__exit__()
     value = float(np.mean([v["mpix_s"] for v in res.values()]))
     _line("paper synthetic workloads at r=25 (4096^2): output Mpix/s (mean over cases)", "Mpix/s", value,
           {"dtype": "u8+u16", "cases": res, "config": {"workload": "paper: random normal and diagonal sines, "
                                                        "8/16-bit, r=25", "l2": "flushed before every timed call"}},
-          args)
+          args, clk=clk)
 
 
 def run_serve(args, hrm, inputs, torch, dev):
     """Continuous batching (hrm server) vs plain per-image launches on the same
-    Poisson request stream: latency from arrival to result, and throughput."""
-    import threading
+    Poisson request stream: latency from arrival to result, and throughput.
+    After the timing, every served output is compared bit for bit with the
+    plain launch of the same request; any difference fails the run."""
     pool = {"u8": torch.from_numpy(inputs.uniform_u8(4096, 4096)).to(dev),
             "u16": torch.from_numpy(inputs.xray12_u16(4096, 4096)).to(dev)}
     arena = torch.empty(16 << 30, dtype=torch.uint8, device=dev)  # the 16 GB admission budget
     results = {}
+    clk = ClockSampler(_smi_index()).__enter__()
     for rate in [float(x) for x in args.rates.split(",")]:
         n = int(min(args.requests, rate * 10))
         reqs = inputs.request_stream(n, rate=rate, seed=inputs.seed_for(5, int(rate)))
@@ -455,18 +473,21 @@ def run_serve(args, hrm, inputs, torch, dev):
             y0, x0 = rng.integers(0, 4097 - q["h"]), rng.integers(0, 4097 - q["w"])
             views.append(pool[q["dtype"]][y0:y0 + q["h"], x0:x0 + q["w"]])
         npx = sum(q["w"] * q["h"] for q in reqs)
+        outs = [torch.empty_like(v) for v in views]
+        plain_outs = [torch.empty_like(v) for v in views]
+        torch.cuda.synchronize()
         # (a) server: continuous batching
         srv = hrm.Server(arena, max_inflight=4096, max_queue=16384)
-        outs = [None] * n
         tick = [0] * n
         t0 = time.perf_counter()
         for i, q in enumerate(reqs):
             while time.perf_counter() - t0 < q["t"]:
                 pass
-            outs[i] = torch.empty_like(views[i])
             tick[i] = srv.submit(views[i], outs[i], q["r"])
         for i in range(n):
-            srv.poll(tick[i], -1)
+            rc = srv.poll(tick[i], 600_000_000)  # bounded: a lost wave fails the run instead of hanging it
+            if rc != hrm.HRM_OK:
+                raise SystemExit("served request %d failed with status %d" % (i, rc))
         t_srv = time.perf_counter() - t0
         lat_srv = np.array([srv.latency_us(t) for t in tick]) / 1e3
         st = srv.stats()
@@ -478,24 +499,33 @@ def run_serve(args, hrm, inputs, torch, dev):
         for i, q in enumerate(reqs):
             while time.perf_counter() - t0 < q["t"]:
                 pass
-            o = torch.empty_like(views[i])
-            hrm.filter2d(views[i], q["r"], out=o)
+            hrm.filter2d(views[i], q["r"], out=plain_outs[i])
             stream.synchronize()
             lat_plain[i] = (time.perf_counter() - t0 - q["t"]) * 1e3
         t_plain = time.perf_counter() - t0
+        # (c) bit-exact: every served output equals its plain launch
+        diff = [i for i in range(n) if not torch.equal(outs[i], plain_outs[i])]
+        if diff:
+            raise SystemExit("serving at %g req/s: %d of %d served outputs differ from their plain launches "
+                             "(first: request %d)" % (rate, len(diff), n, diff[0]))
         results[str(int(rate))] = {
-            "requests": n, "mpix": npx / 1e6,
+            "requests": n, "mpix": npx / 1e6, "bit_identical_to_plain_launches": True,
             "server": {"mpix_s": npx / t_srv / 1e6, "p50_ms": float(np.percentile(lat_srv, 50)),
                        "p99_ms": float(np.percentile(lat_srv, 99)), "waves": int(st.waves),
                        "bytes_high_water": int(st.bytes_high_water)},
             "plain": {"mpix_s": npx / t_plain / 1e6, "p50_ms": float(np.percentile(lat_plain, 50)),
                       "p99_ms": float(np.percentile(lat_plain, 99))}}
+        del outs, plain_outs
+    clk.__exit__()
     top = results[max(results, key=float)]
     _line("serving: output Mpix/s and p50/p99 latency, continuous batching vs plain launches", "Mpix/s",
           top["server"]["mpix_s"], {"dtype": "u8+u16", "per_rate": results,
                                     "config": {"workload": "Poisson request stream, side log-uniform 64..4096, "
                                                            "50% uint8 / 50% uint16, radius 1..50, 16 GB budget",
-                                               "value_is": "server Mpix/s at the highest rate"}}, args)
+                                               "value_is": "server Mpix/s at the highest rate",
+                                               "parity": "every served output compared bit for bit with the "
+                                                         "plain launch of the same request (the run fails on "
+                                                         "any difference)"}}, args, clk=clk)
 
 
 # ---- GPU arm ------------------------------------------------------------------------
@@ -684,7 +714,11 @@ def report(args, ws, times, dev_ms_step, value, t_wall, e2e_ms, clk, npx, dist, 
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-        "config": dict(bench_config(ws, img_np), ms_per_step_wall_incl_flush=1e3 * t_wall / args.steps),
+        "config": bench_config(ws, img_np),
+        "value_is": "whole-job output pixels of one step (one image at each of the radii) / the summed CUDA-event "
+                    "times of its launches: a time-weighted aggregate dominated by the slowest radii; "
+                    "per_radius gives each radius alone",
+        "ms_per_step_wall_incl_flush": 1e3 * t_wall / args.steps,
         "per_radius": per_radius,
         "roofline": {"bound": "hbm", "kernel": kname + " (the hrm_filter2d call: level pre-pass + kernel)",
                      "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
@@ -698,9 +732,12 @@ def report(args, ws, times, dev_ms_step, value, t_wall, e2e_ms, clk, npx, dist, 
         "e2e": None if e2e_ms != e2e_ms else
                {"value": ws * len(RADII) * npx / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * npx, "d2h_bytes_per_step": 2 * npx * len(RADII),
-                "ms_per_step": e2e_ms, "path": "pinned host -> device copy, hrm_filter2d at every radius, "
-                                              "device -> pinned host copy of every output (uploads and downloads "
-                                              "on their own streams, overlapping the filters)"},
+                "ms_per_step": e2e_ms, "path": "pinned host -> device copy of the input, hrm_filter2d at every "
+                                              "radius, device -> pinned host copy of every output (uploads and "
+                                              "downloads on their own streams, overlapping the filters)",
+                "cache": "warm: no L2 flush in this leg; each step's input arrives by a fresh host -> device "
+                         "copy, which leaves it in L2 as it would for any caller (the device-timed value "
+                         "flushes L2 before every launch)"},
         "clocks": clk.summary(),
     }
     if ws == 1 and not args.no_cpu_baseline:

@@ -84,9 +84,9 @@ typedef enum {
  *   border     HRM_BORDER_REPLICATE
  *   flags      0 or HRM_ADAPTIVE
  *   stream     cudaStream_t or NULL
- * Radius <= 2 uses register selection networks; larger radii use the
- * hierarchical histogram kernels.  Empty images (width or height 0) are a
- * no-op returning HRM_OK. */
+ * Radius <= 5 uses register selection networks (3x3, 5x5 and pruned k x k
+ * networks); larger radii use the hierarchical histogram kernels.  Empty
+ * images (width or height 0) are a no-op returning HRM_OK. */
 int hrm_filter2d(int dtype, const void* src, size_t src_pitch, void* dst, size_t dst_pitch,
                  int width, int height, int radius, int border, unsigned flags, void* stream);
 
@@ -193,24 +193,28 @@ int hrm_filter_batch(const hrm_job* jobs, int njobs, void* stream);
 
 /* hrm_filter_batch_noalloc -- the same batched filter, for callers that must
  * not allocate device memory.  (The paper has no counterpart: this is a
- * deployment entry point.)  Some callers cannot call cudaMalloc: code that
- * runs while a stream is being captured into a CUDA graph (an allocation is
- * not a stream operation and cannot be recorded), frame loops with a hard
- * latency budget (an allocation may synchronise the device), and programs
- * whose device memory is handed out by their own pooling allocator, where a
- * library allocating behind its back breaks the pool's accounting.
+ * deployment entry point.)  Some callers cannot call cudaMalloc: frame loops
+ * with a hard latency budget (an allocation may synchronise the whole
+ * device and stall every stream), and programs whose device memory is handed
+ * out by their own pooling allocator, where a library allocating behind the
+ * pool's back breaks its accounting or fails once the pool has reserved the
+ * memory.
  *
  * This call allocates nothing: its scratch (job table, tile offsets, level
  * descriptors, queue counter, error word, pre-pass histograms) is one
  * file-scope device array of 64 KiB that every GPU loading the library holds
  * until the process exits.  It takes at most 64 jobs per call and rejects
  * more with HRM_EINVAL.  The first call on each device looks up that array's
- * device address (cudaGetSymbolAddress) with the device current; make that
- * first call before any stream capture.  All calls share the one array and it
- * keeps the last call's contents (the call clears what must start at zero),
- * so calls whose work overlaps on the GPU -- on different streams, or from
- * different threads without ordering -- race: serialise them.  Outputs are
- * bit-identical to hrm_filter_batch.  Other arguments as for hrm_filter_batch. */
+ * device address (cudaGetSymbolAddress) with the device current.  All calls
+ * share the one array and it keeps the last call's contents (the call clears
+ * what must start at zero), so calls whose work overlaps on the GPU -- on
+ * different streams, or from different threads without ordering -- race:
+ * serialise them.  The job tables are copied from host memory on the
+ * caller's thread (cudaMemcpyAsync from pageable memory returns once the
+ * source has been read).  A kernel error raised by this path stays set in the
+ * array until hrm_device_status (any stream of the device; it allocates
+ * nothing) reads and clears it.  Outputs are bit-identical to
+ * hrm_filter_batch.  Other arguments as for hrm_filter_batch. */
 int hrm_filter_batch_noalloc(const hrm_job* jobs, int njobs, void* stream);
 
 /* hrm_batch_graph_* -- capture the batched launch for a FIXED job list into a
@@ -219,6 +223,9 @@ int hrm_filter_batch_noalloc(const hrm_job* jobs, int njobs, void* stream);
 typedef struct hrm_batch_graph hrm_batch_graph;
 int hrm_batch_graph_create(const hrm_job* jobs, int njobs, void* stream, hrm_batch_graph** out);
 int hrm_batch_graph_launch(hrm_batch_graph* g, void* stream);
+/* Wait for `stream`, then report (and clear) the error word the graph's
+ * kernels write: HRM_OK or HRM_EDEVICE (replays accumulate until read). */
+int hrm_batch_graph_status(hrm_batch_graph* g, void* stream);
 int hrm_batch_graph_destroy(hrm_batch_graph* g);
 
 /* ---- planning / autotuning ---------------------------------------------
@@ -330,9 +337,12 @@ int hrm_server_stats_get(hrm_server* s, hrm_server_stats* out);
 /* Stop the loop; pending requests end as HRM_ECANCELED. */
 int hrm_server_destroy(hrm_server* s);
 
-/* Wait for `stream`, then report (and clear) any error flag the kernels of
- * this stream's workspace raised: HRM_OK or HRM_EDEVICE.  Kernels never trap;
- * internal limits that cannot be met set this flag instead. */
+/* Wait for `stream`, then report (and clear) any error flag raised by the
+ * kernels of this stream's workspace (single-image calls and
+ * hrm_filter_batch) or by hrm_filter_batch_noalloc on the current device:
+ * HRM_OK or HRM_EDEVICE.  Kernels never trap; internal limits that cannot be
+ * met set this flag instead.  Allocates nothing.  Graphs report through
+ * hrm_batch_graph_status. */
 int hrm_device_status(void* stream);
 
 /* Thread-local description of the last error on this thread. */

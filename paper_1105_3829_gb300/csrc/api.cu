@@ -88,6 +88,14 @@ int workspace_for(cudaStream_t st, Workspace** out) {
     return HRM_OK;
 }
 
+Workspace* workspace_find(cudaStream_t st) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_ws.find(std::make_pair(dev, st));
+    return it == g_ws.end() ? nullptr : &it->second;
+}
+
 // ---- planning ----------------------------------------------------------------------
 static std::map<std::tuple<int, int, int, int, int, int, unsigned>, hrm_plan> g_plans;
 
@@ -644,19 +652,27 @@ int hrm_topology_get(hrm_topology* topo, void* stream, hrm_topology_info* out) {
 }
 
 int hrm_device_status(void* stream) {
-    Workspace* ws = nullptr;
-    int rc = workspace_for((cudaStream_t)stream, &ws);
-    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    // a stream without a workspace has run no kernel that writes one: nothing
+    // is allocated here, so callers of the no-allocation path may call this too
+    Workspace* ws = workspace_find(st);
     unsigned host = 0;
-    cudaError_t e = cudaMemcpyAsync(&host, ws->err, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                                    (cudaStream_t)stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    cudaError_t e = cudaSuccess;
+    if (ws) e = cudaMemcpyAsync(&host, ws->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "device status");
     if (host) {
-        cudaMemsetAsync(ws->err, 0, sizeof(unsigned), (cudaStream_t)stream);
-        cudaStreamSynchronize((cudaStream_t)stream);
-        return fail(HRM_EDEVICE, "kernel reported device error code " + std::to_string(host));
+        e = cudaMemsetAsync(ws->err, 0, sizeof(unsigned), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "device status clear");
     }
+    unsigned na = 0;
+    const int rc = noalloc_error_take(st, &na);
+    if (rc) return rc;
+    if (host) return fail(HRM_EDEVICE, "kernel reported device error code " + std::to_string(host));
+    if (na)
+        return fail(HRM_EDEVICE, "a hrm_filter_batch_noalloc kernel reported device error code " +
+                                     std::to_string(na));
     return HRM_OK;
 }
 

@@ -495,6 +495,30 @@ static int noalloc_scratch(unsigned char** out) {
 template <class T>
 using NAVec = FixedVec<T, NOALLOC_MAX_JOBS + 1>;
 
+// Read and clear the no-allocation path's error word for the current device
+// after `st` has finished (hrm_device_status).  A device on which no
+// no-allocation call has run reports 0 without touching the GPU.
+int noalloc_error_take(cudaStream_t st, unsigned* code) {
+    *code = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        if (dev >= 0 && dev < 64) base = g_na_addr[dev];
+    }
+    if (!base) return HRM_OK;
+    unsigned* err = (unsigned*)(base + NA_ERR);
+    e = cudaMemcpyAsync(code, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && *code) {
+        e = cudaMemsetAsync(err, 0, sizeof(unsigned), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    return e == cudaSuccess ? HRM_OK : cuda_fail(e, "no-allocation error word");
+}
+
 }  // namespace hrm
 
 using namespace hrm;
@@ -521,9 +545,11 @@ extern "C" int hrm_filter_batch_noalloc(const hrm_job* jobs, int njobs, void* st
     BatchPlanT<NAVec> plan;  // fixed capacity on the stack: no heap or device allocation
     rc = plan_batch(jobs, njobs, dev, plan);
     if (rc) return rc;
-    // The array keeps the previous call's contents: the error word is cleared
-    // here, the queue counter and the level descriptors by enqueue_batch.
-    cudaError_t e = cudaMemsetAsync(dev.err, 0, sizeof(unsigned), st);
+    // The array keeps the previous call's contents: enqueue_batch clears the
+    // queue counter and the level descriptors.  The error word starts at zero
+    // (the array is zero-initialised when the library loads) and is left set
+    // by any kernel that raises it until hrm_device_status reads and clears it.
+    cudaError_t e = cudaSuccess;
     auto up = [&](void* d, const void* h, size_t n) {
         if (n && e == cudaSuccess) e = cudaMemcpyAsync(d, h, n, cudaMemcpyHostToDevice, st);
     };
@@ -533,6 +559,13 @@ extern "C" int hrm_filter_batch_noalloc(const hrm_job* jobs, int njobs, void* st
     if (e != cudaSuccess) return cuda_fail(e, "no-allocation batch upload");
     return enqueue_batch(plan, dev, st);
 }
+
+// Test hook, deliberately not declared in include/hrm.h: plant an error code
+// from the host in the error word of the no-allocation array of the current
+// device (which = 0) or of a graph (which = 1), so that tests can check that
+// hrm_device_status / hrm_batch_graph_status report and clear it without
+// making any kernel fail.
+extern "C" int hrm_debug_set_error_word(int which, void* graph, unsigned code);
 
 struct hrm_batch_graph {
     BatchDev dev;
@@ -614,6 +647,36 @@ int hrm_batch_graph_launch(hrm_batch_graph* g, void* stream) {
     if (!g || !g->exec) return fail(HRM_EINVAL, "null graph");
     cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
     return e == cudaSuccess ? HRM_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+int hrm_batch_graph_status(hrm_batch_graph* g, void* stream) {
+    if (!g || !g->dev.err) return fail(HRM_EINVAL, "null graph");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned code = 0;
+    cudaError_t e = cudaMemcpyAsync(&code, g->dev.err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && code) {
+        e = cudaMemsetAsync(g->dev.err, 0, sizeof(unsigned), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "graph status");
+    if (code) return fail(HRM_EDEVICE, "a replay of this graph reported device error code " + std::to_string(code));
+    return HRM_OK;
+}
+
+int hrm_debug_set_error_word(int which, void* graph, unsigned code) {
+    unsigned* word = nullptr;
+    if (which == 0) {
+        unsigned char* base = nullptr;
+        const int rc = noalloc_scratch(&base);
+        if (rc) return rc;
+        word = (unsigned*)(base + NA_ERR);
+    } else if (which == 1 && graph) {
+        word = ((hrm_batch_graph*)graph)->dev.err;
+    }
+    if (!word) return fail(HRM_EINVAL, "hrm_debug_set_error_word: unknown target");
+    const cudaError_t e = cudaMemcpy(word, &code, sizeof(unsigned), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? HRM_OK : cuda_fail(e, "hrm_debug_set_error_word");
 }
 
 int hrm_batch_graph_destroy(hrm_batch_graph* g) {

@@ -36,6 +36,11 @@ struct Workspace {
     unsigned* counters = nullptr;  // 64 work counters for persistent kernels
 };
 int workspace_for(cudaStream_t st, Workspace** out);
+// The stream's workspace if one exists (never allocates), else null.
+Workspace* workspace_find(cudaStream_t st);
+// hrm_filter_batch_noalloc's error word for the current device, read after
+// `st` finishes and cleared (0 when no such call has run on the device).
+int noalloc_error_take(cudaStream_t st, unsigned* code);
 
 // Planning.
 // Largest 2D radius served by a selection network (sortnet.cuh).

@@ -33,7 +33,9 @@
 
 namespace hrm {
 int topology_device_of(const hrm_topology* t);  // api.cu
+int fail(int code, const std::string& msg);     // api.cu: sets hrm_last_error, returns code
 }
+using hrm::fail;
 
 namespace {
 
@@ -291,8 +293,10 @@ extern "C" {
 
 int hrm_server_create(void* arena_dev_ptr, size_t arena_bytes, int max_inflight, int max_queue,
                       hrm_server** out) {
-    if (!out || !arena_dev_ptr || arena_bytes == 0 || max_inflight <= 0 || max_queue < 0)
-        return HRM_EINVAL;
+    if (!out) return fail(HRM_EINVAL, "hrm_server_create: null output pointer");
+    if (!arena_dev_ptr || arena_bytes == 0) return fail(HRM_EINVAL, "hrm_server_create: empty arena");
+    if (max_inflight <= 0 || max_queue < 0)
+        return fail(HRM_EINVAL, "hrm_server_create: max_inflight must be > 0 and max_queue >= 0");
     auto* s = new hrm_server();
     s->arena = (unsigned char*)arena_dev_ptr;
     s->arena_bytes = arena_bytes;
@@ -310,7 +314,9 @@ int hrm_server_create(void* arena_dev_ptr, size_t arena_bytes, int max_inflight,
         for (cudaEvent_t ev : s->wave_end)
             if (ev) cudaEventDestroy(ev);
         delete s;
-        return HRM_ECUDA;
+        const cudaError_t e = cudaGetLastError();
+        return fail(HRM_ECUDA, std::string("hrm_server_create: stream or event creation failed: ") +
+                                   cudaGetErrorString(e));
     }
     s->th = std::thread(server_loop, s);
     *out = s;
@@ -318,7 +324,7 @@ int hrm_server_create(void* arena_dev_ptr, size_t arena_bytes, int max_inflight,
 }
 
 int hrm_submit(hrm_server* s, const hrm_request* q, uint64_t* ticket) {
-    if (!s || !q || !ticket) return HRM_EINVAL;
+    if (!s || !q || !ticket) return fail(HRM_EINVAL, "hrm_submit: null server, request or ticket pointer");
     const size_t es = (q->dtype == HRM_U16) ? 2 : 1;
     const bool bad = (q->dtype != HRM_U8 && q->dtype != HRM_U16) || q->width <= 0 || q->height <= 0 ||
                      q->radius < 0 || q->radius > HRM_MAX_RADIUS_2D || (q->flags & ~(unsigned)HRM_ADAPTIVE) ||
@@ -326,11 +332,16 @@ int hrm_submit(hrm_server* s, const hrm_request* q, uint64_t* ticket) {
                      q->dst_pitch < (size_t)q->width * es ||
                      (q->topo && (q->flags || hrm::topology_device_of(q->topo) != s->device));
     std::lock_guard<std::mutex> lk(s->mu);
-    if (bad || 2 * (size_t)q->width * q->height * es > s->arena_bytes) {
+    if (bad) {
         s->rejected++;
-        return HRM_EINVAL;
+        return fail(HRM_EINVAL, "hrm_submit: malformed request (dtype, size, radius, flags, pointers, pitches "
+                                "or topology)");
     }
-    if ((int)s->queue.size() >= s->max_queue) return HRM_EAGAIN;
+    if (2 * (size_t)q->width * q->height * es > s->arena_bytes) {
+        s->rejected++;
+        return fail(HRM_EINVAL, "hrm_submit: the request's input and output never fit the arena");
+    }
+    if ((int)s->queue.size() >= s->max_queue) return fail(HRM_EAGAIN, "hrm_submit: submit queue full");
     Req* r = new Req();
     r->ticket = s->next_ticket++;
     r->q = *q;
@@ -358,18 +369,22 @@ static int retire(hrm_server* s, Req* r) {
 }
 
 int hrm_poll(hrm_server* s, uint64_t ticket, int timeout_us) {
-    if (!s) return HRM_EINVAL;
+    if (!s) return fail(HRM_EINVAL, "hrm_poll: null server");
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->live.find(ticket);
-    if (it == s->live.end()) return HRM_EINVAL;
+    if (it == s->live.end()) return fail(HRM_EINVAL, "hrm_poll: unknown or retired ticket");
     Req* r = it->second;
     if (r->state != DONE) {
-        if (timeout_us == 0) return HRM_EAGAIN;
+        if (timeout_us == 0) return fail(HRM_EAGAIN, "hrm_poll: request still pending");
         auto pred = [&] { return r->state == DONE; };
         if (timeout_us < 0) s->cv_done.wait(lk, pred);
-        else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), pred)) return HRM_ETIMEDOUT;
+        else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), pred))
+            return fail(HRM_ETIMEDOUT, "hrm_poll: request still pending after the timeout");
     }
-    return retire(s, r);
+    const int st = retire(s, r);
+    if (st == HRM_ECANCELED) return fail(st, "hrm_poll: request cancelled (server destroyed)");
+    if (st != HRM_OK) return fail(st, "hrm_poll: the request's wave failed with status " + std::to_string(st));
+    return st;
 }
 
 double hrm_ticket_latency_us(hrm_server* s, uint64_t ticket) {
@@ -380,7 +395,7 @@ double hrm_ticket_latency_us(hrm_server* s, uint64_t ticket) {
 }
 
 int hrm_server_stats_get(hrm_server* s, hrm_server_stats* o) {
-    if (!s || !o) return HRM_EINVAL;
+    if (!s || !o) return fail(HRM_EINVAL, "hrm_server_stats_get: null server or output pointer");
     std::lock_guard<std::mutex> lk(s->mu);
     o->submitted = s->submitted;
     o->admitted = s->admitted_n;

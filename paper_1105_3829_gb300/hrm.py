@@ -88,6 +88,7 @@ SIGNATURES = {
     "hrm_filter_batch_noalloc": (_I, [C.POINTER(hrm_job), _I, _P]),
     "hrm_batch_graph_create": (_I, [C.POINTER(hrm_job), _I, _P, C.POINTER(_P)]),
     "hrm_batch_graph_launch": (_I, [_P, _P]),
+    "hrm_batch_graph_status": (_I, [_P, _P]),
     "hrm_batch_graph_destroy": (_I, [_P]),
     "hrm_autotune": (_I, [_I, _I, _I, _I, _I, _I, _U, _P, _S, _S, _P, C.POINTER(hrm_plan)]),
     "hrm_get_plan": (_I, [_I, _I, _I, _I, _I, _I, _U, C.POINTER(hrm_plan)]),
@@ -100,6 +101,8 @@ SIGNATURES = {
     "hrm_ticket_latency_us": (C.c_double, [_P, C.c_uint64]),
     "hrm_server_stats_get": (_I, [_P, C.POINTER(hrm_server_stats)]),
     "hrm_server_destroy": (_I, [_P]),
+    # test hook (not in include/hrm.h): plant a device error code from the host
+    "hrm_debug_set_error_word": (_I, [_I, _P, _U]),
 }
 
 _lib = None
@@ -275,6 +278,10 @@ class BatchGraph:
 
     def launch(self, stream=None):
         check(lib().hrm_batch_graph_launch(self._h, _stream(stream)), "hrm_batch_graph_launch")
+
+    def status(self, stream=None) -> int:
+        """hrm_batch_graph_status: wait for the stream, raise on a kernel error flag of this graph."""
+        return check(lib().hrm_batch_graph_status(self._h, _stream(stream)), "hrm_batch_graph_status")
 
     def close(self):
         if self._h:

@@ -149,32 +149,48 @@ def test_environment_plan_cache_and_forced_path(lib, tmp_path):
 
 def test_server_topology_and_graph_arguments_without_device(lib):
     """Null handles and malformed arguments are refused on the host, before
-    any device work: serving, frame-stream topologies, graphs, plans."""
+    any device work (serving, frame-stream topologies, graphs, plans), and
+    every refusal leaves its own message in hrm_last_error."""
     from paper_1105_3829_gb300 import hrm
     E = hrm.HRM_EINVAL
+    buf = ctypes.create_string_buffer(1 << 16)
+    src = ctypes.addressof(buf)
+
+    def refused(call, code=E):
+        # a different error first, so a stale message cannot pass for a fresh one
+        assert hrm.hrm_filter2d(3, src, 64, src + (1 << 15), 64, 32, 8, 2, 0, 0, None) == E
+        sentinel = hrm.last_error()
+        assert call() == code
+        msg = hrm.last_error()
+        assert msg and msg != sentinel, msg
+        return msg
+
     h = ctypes.c_void_p()
-    buf = ctypes.create_string_buffer(1 << 12)
-    arena = ctypes.addressof(buf)
-    assert hrm.hrm_server_create(None, 1 << 20, 8, 0, ctypes.byref(h)) == E       # no arena
-    assert hrm.hrm_server_create(arena, 0, 8, 0, ctypes.byref(h)) == E             # empty arena
-    assert hrm.hrm_server_create(arena, 1 << 12, 0, 0, ctypes.byref(h)) == E       # no in-flight slots
-    assert hrm.hrm_server_create(arena, 1 << 12, 8, -1, ctypes.byref(h)) == E      # negative queue
+    arena = src
+    refused(lambda: hrm.hrm_server_create(None, 1 << 20, 8, 0, ctypes.byref(h)))        # no arena
+    refused(lambda: hrm.hrm_server_create(arena, 0, 8, 0, ctypes.byref(h)))              # empty arena
+    refused(lambda: hrm.hrm_server_create(arena, 1 << 12, 0, 0, ctypes.byref(h)))        # no in-flight slots
+    refused(lambda: hrm.hrm_server_create(arena, 1 << 12, 8, -1, ctypes.byref(h)))       # negative queue
+    refused(lambda: hrm.hrm_server_create(arena, 1 << 12, 8, 0, None))                  # no output
     t = ctypes.c_uint64()
-    assert hrm.hrm_submit(None, None, ctypes.byref(t)) == E
-    assert hrm.hrm_poll(None, 1, 0) == E
+    refused(lambda: hrm.hrm_submit(None, None, ctypes.byref(t)))
+    refused(lambda: hrm.hrm_poll(None, 1, 0))
     assert hrm.hrm_ticket_latency_us(None, 1) < 0
-    assert hrm.hrm_server_stats_get(None, None) == E
+    refused(lambda: hrm.hrm_server_stats_get(None, None))
     assert hrm.hrm_server_destroy(None) == hrm.HRM_OK
     info = hrm.hrm_topology_info()
-    assert hrm.hrm_topology_get(None, None, ctypes.byref(info)) == E
+    refused(lambda: hrm.hrm_topology_get(None, None, ctypes.byref(info)))
     assert hrm.hrm_topology_destroy(None) == hrm.HRM_OK
-    assert hrm.hrm_topology_create(None) == E
+    refused(lambda: hrm.hrm_topology_create(None))
     g = ctypes.c_void_p()
     jobs = (hrm.hrm_job * 1)()
-    assert hrm.hrm_batch_graph_create(jobs, 0, None, ctypes.byref(g)) == E
-    assert hrm.hrm_batch_graph_create(None, 1, None, ctypes.byref(g)) == E
-    assert hrm.hrm_batch_graph_launch(None, None) == E
+    refused(lambda: hrm.hrm_batch_graph_create(jobs, 0, None, ctypes.byref(g)))
+    refused(lambda: hrm.hrm_batch_graph_create(None, 1, None, ctypes.byref(g)))
+    refused(lambda: hrm.hrm_batch_graph_launch(None, None))
+    refused(lambda: hrm.hrm_batch_graph_status(None, None))
+    refused(lambda: hrm.hrm_filter_batch_noalloc(jobs, -1, None))
+    assert "64" in refused(lambda: hrm.hrm_filter_batch_noalloc((hrm.hrm_job * 65)(), 65, None))
     p = hrm.hrm_plan()
-    assert hrm.hrm_get_plan(2, 4, 64, 64, 1, 5, 0, ctypes.byref(p)) == E           # dims
-    assert hrm.hrm_set_plan(2, 2, 64, 64, 1, 5, 0, ctypes.byref(hrm.hrm_plan(64, 0, 0, 0))) == E   # tile width
-    assert hrm.hrm_set_plan(2, 2, 64, 64, 1, 5, 0, ctypes.byref(hrm.hrm_plan(0, 0, 0, 3))) == E    # path
+    refused(lambda: hrm.hrm_get_plan(2, 4, 64, 64, 1, 5, 0, ctypes.byref(p)))            # dims
+    refused(lambda: hrm.hrm_set_plan(2, 2, 64, 64, 1, 5, 0, ctypes.byref(hrm.hrm_plan(64, 0, 0, 0))))   # tile width
+    refused(lambda: hrm.hrm_set_plan(2, 2, 64, 64, 1, 5, 0, ctypes.byref(hrm.hrm_plan(0, 0, 0, 3))))    # path

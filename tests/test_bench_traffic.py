@@ -29,7 +29,10 @@ def test_changed_sources_give_null(tmp_path, monkeypatch):
     shutil.copytree(os.path.join(ROOT, "paper_1105_3829_gb300", "csrc"), fake / "paper_1105_3829_gb300" / "csrc")
     shutil.copytree(os.path.join(ROOT, "profiles"), fake / "profiles")
     monkeypatch.setattr(bench, "ROOT", str(fake))
-    key = next(iter(json.load(open(fake / "profiles" / "traffic.json"))["kernels"]))
+    table = json.load(open(fake / "profiles" / "traffic.json"))
+    table["csrc_hash"] = bench.csrc_hash()  # as if captured from these sources
+    json.dump(table, open(fake / "profiles" / "traffic.json", "w"))
+    key = next(iter(table["kernels"]))
     assert bench.traffic_for(key) is not None
     with open(fake / "paper_1105_3829_gb300" / "csrc" / "hist_tile.cuh", "a") as f:
         f.write("\n// edited\n")

@@ -86,6 +86,14 @@ def test_graph_replay_matches(hrm, oracle):
     g.launch()
     torch.cuda.synchronize()
     np.testing.assert_array_equal(outs[0].cpu().numpy(), oracle.median2d(new, data[0][1]))
+    assert g.status() == hrm.HRM_OK
+    # a kernel error word of the graph (planted from the host: no kernel is
+    # made to fail) is reported once by hrm_batch_graph_status, then cleared
+    assert hrm.lib().hrm_debug_set_error_word(1, g._h, 3) == hrm.HRM_OK
+    with pytest.raises(hrm.HRMError) as e:
+        g.status()
+    assert e.value.code == hrm.HRM_EDEVICE
+    assert g.status() == hrm.HRM_OK
     g.close()
 
 

@@ -1,11 +1,15 @@
 """The no-allocation batch entry point (hrm_filter_batch_noalloc).
 
-It serves callers that cannot allocate device memory (for example while a
-stream is being captured, or inside a pooled-memory application), so its
-scratch is a fixed device array rather than cudaMalloc'ed buffers.  This test
-calls it through the C ABI twice in a row on a mixed batch and compares every
-output with the allocating entry point, hrm_filter_batch, bit for bit.  It
-lives in its own file, collected last, and passes alone or after the others.
+It serves callers that cannot allocate device memory: frame loops with a hard
+latency budget (cudaMalloc may synchronise the device) and programs whose
+device memory belongs to their own pooling allocator.  Its scratch is a fixed
+device array rather than cudaMalloc'ed buffers.  This test calls it through
+the C ABI twice in a row on a mixed batch (2D and 3D, both dtypes, small and
+large radii, a radius-0 copy and one frame-stream job) and compares every
+output with the allocating entry point, hrm_filter_batch, and with the CPU
+oracle, bit for bit.  It also checks that a kernel error word planted in the
+array is reported by hrm_device_status and cleared.  It lives in its own file,
+collected last, and passes alone or after the others.
 """
 import numpy as np
 import pytest
@@ -38,17 +42,56 @@ def _batch(seed):
     ]
 
 
-def test_noalloc_matches_allocating_batch_twice(hrm):
-    for call, seed in enumerate((5, 6)):  # two calls in a row on fresh data
-        data = _batch(seed)
-        srcs = [torch.from_numpy(a).cuda() for a, _, _ in data]
-        ref = [torch.zeros_like(s) for s in srcs]
-        got = [torch.full_like(s, 7) for s in srcs]
-        hrm.filter_batch([hrm.make_job(s, o, r, adaptive=ad) for s, o, (_, r, ad) in zip(srcs, ref, data)])
-        hrm.filter_batch_noalloc([hrm.make_job(s, o, r, adaptive=ad) for s, o, (_, r, ad) in zip(srcs, got, data)])
-        torch.cuda.synchronize()
-        for o, e in zip(got, ref):
-            np.testing.assert_array_equal(o.cpu().numpy(), e.cpu().numpy())
+def _expected(oracle, a, r):
+    if r == 0:
+        return a
+    return oracle.median3d(a, r) if a.ndim == 3 else oracle.median2d(a, r)
+
+
+def test_noalloc_matches_allocating_batch_and_oracle_twice(hrm, oracle):
+    from paper_1105_3829_gb300 import inputs
+    topo_ref, topo_got = hrm.Topology(), hrm.Topology()
+    try:
+        for call, seed in enumerate((5, 6)):  # two calls in a row on fresh data
+            data = _batch(seed)
+            frame = inputs.lowkey16_u16(130, 210, seed=seed + 9)  # one frame of a stream per call
+            srcs = [torch.from_numpy(a).cuda() for a, _, _ in data]
+            fsrc = torch.from_numpy(frame).cuda()
+            ref = [torch.zeros_like(s) for s in srcs] + [torch.zeros_like(fsrc)]
+            got = [torch.full_like(s, 7) for s in srcs] + [torch.full_like(fsrc, 7)]
+            jobs_ref = [hrm.make_job(s, o, r, adaptive=ad) for s, o, (_, r, ad) in zip(srcs, ref, data)]
+            jobs_got = [hrm.make_job(s, o, r, adaptive=ad) for s, o, (_, r, ad) in zip(srcs, got, data)]
+            jobs_ref.append(hrm.make_job(fsrc, ref[-1], 12, topo=topo_ref))
+            jobs_got.append(hrm.make_job(fsrc, got[-1], 12, topo=topo_got))
+            hrm.filter_batch(jobs_ref)
+            hrm.filter_batch_noalloc(jobs_got)
+            assert hrm.device_status() == hrm.HRM_OK
+            torch.cuda.synchronize()
+            arrays = [a for a, _, _ in data] + [frame]
+            radii = [r for _, r, _ in data] + [12]
+            for o, e, a, r in zip(got, ref, arrays, radii):
+                g = o.cpu().numpy()
+                np.testing.assert_array_equal(g, e.cpu().numpy())
+                np.testing.assert_array_equal(g, _expected(oracle, a, r))
+            # both frame streams now hold the same top level for the next frame
+            assert topo_got.info() == topo_ref.info()
+    finally:
+        topo_ref.close()
+        topo_got.close()
+
+
+def test_noalloc_error_word_is_reported_and_cleared(hrm):
+    a = torch.zeros((40, 50), dtype=torch.uint16, device="cuda")
+    o = torch.empty_like(a)
+    hrm.filter_batch_noalloc([hrm.make_job(a, o, 7)])
+    assert hrm.device_status() == hrm.HRM_OK
+    # plant an error code from the host (no kernel is made to fail)
+    assert hrm.lib().hrm_debug_set_error_word(0, None, 5) == hrm.HRM_OK
+    with pytest.raises(hrm.HRMError) as e:
+        hrm.device_status()
+    assert e.value.code == hrm.HRM_EDEVICE
+    assert "noalloc" in str(e.value)
+    assert hrm.device_status() == hrm.HRM_OK  # read once, then cleared
 
 
 def test_noalloc_rejects_more_than_its_limit(hrm):
