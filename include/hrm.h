@@ -231,8 +231,12 @@ int hrm_batch_graph_destroy(hrm_batch_graph* g);
 /* ---- planning / autotuning ---------------------------------------------
  *
  * The hierarchical kernels are parameterised by tile width (output columns
- * per 4-warp tile), strip length (rows or slices walked per tile) and the
- * shared memory per tile for cached tree nodes.  hrm_autotune times candidate plans
+ * per 4-warp tile: 128 or 256, i.e. one or two outputs per thread), strip
+ * length (rows or slices walked per tile) and the shared memory per tile for
+ * cached tree nodes.  The tree itself is 16-ary at every level (one 16-byte
+ * counter record per node and column): its shape comes from the data (the
+ * uniform tree of the image's bit depth, or the adaptive top level), not from
+ * the plan.  hrm_autotune times candidate plans
  * for one problem class on `stream` and caches the fastest; later calls of
  * the same class (dtype, dims, size, radius, flags) use it.  The timing runs
  * on `sample` (device pointer, the caller's pitches) when it is not NULL --
@@ -248,13 +252,14 @@ int hrm_batch_graph_destroy(hrm_batch_graph* g);
  *
  * Node-cache feedback (2D single-image calls of a class with no set, tuned
  * or forced plan): the first call counts how many tree nodes its tiles had to
- * build and copies the count back asynchronously; once that copy has landed
- * (a non-blocking check at a later call of the class), a class whose tile rows
- * built more than 0.75 nodes on average tries as many cached nodes as fit in
- * up to 200 KB per tile (one or two tiles per SM) instead of the default four
- * tiles per SM; that trial call is counted too, and the class keeps the large
- * cache only if it cut the node builds at least 3-fold.  Nothing waits for
- * the counts.  hrm_get_plan reports the plan a single call of the class
+ * build and copies the count back asynchronously; the second call of the
+ * class waits for that 4-byte copy and, if the tile rows built more than 0.75
+ * nodes on average, tries as many cached nodes as fit in up to 200 KB per
+ * tile (one or two tiles per SM) instead of the default four tiles per SM;
+ * that trial call is counted too, the third call waits for its count, and the
+ * class keeps the large cache only if it cut the node builds at least
+ * 3-fold.  From the third call on, every call of the class runs the same
+ * settled plan.  hrm_get_plan reports the plan a single call of the class
  * would use now, feedback included. */
 typedef struct {
     int tile_width;     /* output columns per tile: 128 or 256 (0 = default) */

@@ -245,12 +245,13 @@ static void apply_plan(PlanH& p, const hrm_plan& hp, int dims, int W, int lines,
 // with either cache and lose by the fewer warps.  Which case a problem class
 // is cannot be seen on the host without reading the image, so the class is
 // measured: its first call counts the node installs of its tiles into a
-// device counter and copies the count back asynchronously.  A later call
-// checks the copy with a non-blocking event query; if a tile row installed
-// more than FB_DEEP_RATE nodes, the next call runs the large-cache plan and is
-// counted the same way, and the class keeps that plan only if it cut the
+// device counter and copies the count back asynchronously.  The second call
+// waits for that copy; if a tile row installed more than FB_DEEP_RATE nodes,
+// it runs the large-cache plan and is counted the same way, the third call
+// waits for that count, and the class keeps the large cache only if it cut the
 // installs at least FB_KEEP_CUT-fold, else it returns to the default for good.
-// Nothing waits, and outputs never depend on the plan.  A set, tuned or
+// From the third call on a class runs one settled plan (stable latency);
+// outputs never depend on the plan.  A set, tuned or
 // forced plan takes precedence and switches the feedback off for its class.
 constexpr int FB_MAX = 4096;             // counters per device
 constexpr double FB_DEEP_RATE = 0.75;    // node installs per tile row that call for a trial
@@ -288,8 +289,11 @@ static bool fb_deep(const ProblemKey& k) {
     if (it == g_fb.end()) return false;
     FbClass& c = it->second;
     if (c.state == 1 || c.state == 4) {
+        // wait for the previous call's 4-byte count: the second call of a
+        // class decides whether to try the large cache, the third whether to
+        // keep it, and every later call runs the settled plan
         const bool clean = cudaPeekAtLastError() == cudaSuccess;
-        const cudaError_t q = cudaEventQuery(c.ev);
+        const cudaError_t q = cudaEventSynchronize(c.ev);
         if (q == cudaSuccess) {
             const double rate = c.rows > 0 ? (double)g_fbdev[dev].h[c.idx] / c.rows : 0.0;
             if (c.state == 1) {
@@ -300,8 +304,10 @@ static bool fb_deep(const ProblemKey& k) {
                 c.deep = rate * FB_KEEP_CUT <= c.rate0;
                 c.state = 2;
             }
-        } else if (clean) {
-            cudaGetLastError();  // a not-ready answer is not an error of a later call
+        } else {
+            if (clean) cudaGetLastError();  // the count is lost: keep the default plan
+            c.state = 2;
+            c.deep = false;
         }
     }
     return c.state == 3 || c.state == 4 || (c.state == 2 && c.deep);

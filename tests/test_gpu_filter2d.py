@@ -281,6 +281,12 @@ def test_node_cache_feedback(hrm, oracle):
             torch.cuda.synchronize()
             np.testing.assert_array_equal(got.cpu().numpy(), want, err_msg="%s call %d" % (name, call))
         after = hrm.get_plan(hrm.HRM_U16, 2, w, h, 1, 15)
+        for call in range(2):  # settled from the third call on: later calls keep the plan
+            hrm.filter2d(src, 15)
+        torch.cuda.synchronize()
+        later = hrm.get_plan(hrm.HRM_U16, 2, w, h, 1, 15)
+        assert (later.tile_width, later.strip_height, later.slot_kbytes) == \
+            (after.tile_width, after.strip_height, after.slot_kbytes), name
         assert before.slot_kbytes < 100, (name, before.slot_kbytes)
         if deep:
             # as many node slots as fit in up to 200 KB (the slot count caps it): one or two tiles per SM
