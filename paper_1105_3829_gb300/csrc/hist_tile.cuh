@@ -307,6 +307,78 @@ __device__ __forceinline__ void deep_update(const Meta& m, unsigned char* slots,
     }
 }
 
+// 2D, 8-bit counters: remove vo and insert vi of column cx in the resident
+// nodes below the root (Section III-B: one +-1 per level), with the level
+// masks held in registers.  Levels 1 and 2 (direct slot tables) are handled
+// together: both values' slot lookups are issued at once, then each touched
+// counter word is bumped.  Deeper levels (16-bit data) take the generic path.
+struct LevelMasks {
+    uint32_t l0, l1, l2;
+    bool deep;  // some resident node lies at level >= 3
+};
+
+__device__ __forceinline__ void pair_update(const Meta& m, const LevelMasks& lm, unsigned char* slots, int NC,
+                                            int cx, uint32_t vo, int co, uint32_t vi, int ci) {
+    const bool ao = (lm.l0 >> co) & 1u, ai = (lm.l0 >> ci) & 1u;
+    if (!ao && !ai) return;
+    int s1o = -1, s1i = -1, s2o = -1, s2i = -1, d1o = 0, d1i = 0, d2o = 0, d2i = 0;
+    int Do = 0, Di = 0;
+    uint32_t uo = 0, ui = 0;
+    if (ao) {
+        uo = vo - m.e[co];
+        Do = (int)m.D[co];
+        const int b1 = min(4, Do);
+        d1o = (int)((uo >> (Do - b1)) & ((1u << b1) - 1u));
+        if ((lm.l1 >> co) & 1u) s1o = m.lut1[co];
+        if (Do > 4 && ((lm.l2 >> co) & 1u)) {
+            const int b2 = min(4, Do - 4);
+            d2o = (int)((uo >> (Do - 4 - b2)) & ((1u << b2) - 1u));
+            s2o = m.lut2[(co << 4) | (int)((uo >> (Do - 4)) & 15u)];
+        }
+    }
+    if (ai) {
+        ui = vi - m.e[ci];
+        Di = (int)m.D[ci];
+        const int b1 = min(4, Di);
+        d1i = (int)((ui >> (Di - b1)) & ((1u << b1) - 1u));
+        if ((lm.l1 >> ci) & 1u) s1i = m.lut1[ci];
+        if (Di > 4 && ((lm.l2 >> ci) & 1u)) {
+            const int b2 = min(4, Di - 4);
+            d2i = (int)((ui >> (Di - 4 - b2)) & ((1u << b2) - 1u));
+            s2i = m.lut2[(ci << 4) | (int)((ui >> (Di - 4)) & 15u)];
+        }
+    }
+    // one 32-bit counter word per (value, level): load, add, store; the two
+    // values' words at one level may coincide (same node), so each update is
+    // a separate read-modify-write in program order
+    auto bump = [&](int sl, int d, int delta) {
+        uint32_t* w = reinterpret_cast<uint32_t*>(slots + ((size_t)sl * NC + cx) * 16) + (d >> 2);
+        const uint32_t inc = 1u << (8 * (d & 3));
+        *w = delta > 0 ? *w + inc : *w - inc;
+    };
+    if (s1o != NO_SLOT && s1o >= 0) bump(s1o, d1o, -1);
+    if (s1i != NO_SLOT && s1i >= 0) bump(s1i, d1i, +1);
+    if (s2o != NO_SLOT && s2o >= 0) bump(s2o, d2o, -1);
+    if (s2i != NO_SLOT && s2i >= 0) bump(s2i, d2i, +1);
+    if (lm.deep) {  // levels >= 3 through the hash of deep nodes
+        for (int q = 0; q < 2; ++q) {
+            const bool act = q ? ai : ao;
+            const int c = q ? ci : co, D = q ? Di : Do;
+            const uint32_t u = q ? ui : uo;
+            if (!act) continue;
+            for (int level = 3; 4 * (level - 1) < D; ++level) {
+                if (!((m.lmask[level] >> c) & 1u)) continue;
+                const int top = D - 4 * (level - 1);
+                const int sl = slot_lookup(m, level, c, u >> top);
+                if (sl < 0) continue;
+                const int b = min(4, top);
+                const int d = (int)((u >> (top - b)) & ((1u << b) - 1u));
+                rec_bump<1>(slots + ((size_t)sl * NC + cx) * 16, d, q ? +1 : -1);
+            }
+        }
+    }
+}
+
 // Block-wide inclusive prefix over columns [lo, hi] of slot s into
 // pfx[1 .. hi-lo+1] (pfx[0] = 0).  The scratch holds two planes of
 // (NC+1) uint4 each -- words 0..3 then words 4..7 of every column -- so that
@@ -585,6 +657,11 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                 // root level: each of the thread's column records is read,
                 // changed by the leaving and entering values, and written back;
                 // all loads are issued before any store
+                LevelMasks lm;
+                lm.l0 = m.lmask[0];
+                lm.l1 = m.lmask[1];
+                lm.l2 = m.lmask[2];
+                lm.deep = m.ndeep != 0;
                 uint32_t vo[CPL], vi[CPL];
                 uint4 rec[CPL];
 #pragma unroll
@@ -607,10 +684,7 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                         delta_add<1>(dw, ci, +1);
                         rec[j].x += dw[0]; rec[j].y += dw[1]; rec[j].z += dw[2]; rec[j].w += dw[3];
                         reinterpret_cast<uint4*>(slots)[cx] = rec[j];
-                        if (vo[j] != vi[j]) {
-                            deep_update<CW>(m, slots, NC, cx, vo[j], co, -1);
-                            deep_update<CW>(m, slots, NC, cx, vi[j], ci, +1);
-                        }
+                        if (vo[j] != vi[j]) pair_update(m, lm, slots, NC, cx, vo[j], co, vi[j], ci);
                     }
                 }
             } else if (to != ti) {
