@@ -445,7 +445,14 @@ def run_paper(args, hrm, inputs, torch, dev, flush):
         for ad in (False, True):
             t = _timed(lambda: hrm.filter2d(img, 25, adaptive=ad, out=out), flush, max(3, args.steps))
             ms = float(np.median(t))
-            res["%s%s" % (name, "_adaptive" if ad else "")] = {"p50_ms": ms, "mpix_s": img.numel() / ms / 1e3}
+            case = {"p50_ms": ms, "mpix_s": img.numel() / ms / 1e3}
+            if name.endswith("16"):  # the node cache's worst case: what hrm_autotune finds for it
+                plan = hrm.autotune(img, 25, adaptive=ad)
+                t2 = _timed(lambda: hrm.filter2d(img, 25, adaptive=ad, out=out), flush, max(3, args.steps))
+                case["autotuned"] = {"p50_ms": float(np.median(t2)), "mpix_s": img.numel() / float(np.median(t2)) / 1e3,
+                                     "plan": {"tile_width": plan.tile_width, "strip_height": plan.strip_height,
+                                              "slot_kbytes": plan.slot_kbytes, "path": plan.path}}
+            res["%s%s" % (name, "_adaptive" if ad else "")] = case
     clk.__exit__()
     value = float(np.mean([v["mpix_s"] for v in res.values()]))
     _line("paper synthetic workloads at r=25 (4096^2): output Mpix/s (mean over cases)", "Mpix/s", value,

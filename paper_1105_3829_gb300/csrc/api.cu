@@ -444,7 +444,9 @@ int make_hist_job(const Image& im, int r, uint32_t K, unsigned flags, int drop_b
     j.tiles_x = (im.W + tw - 1) / tw;
     const int nstrips = strip_layout(walk, p.sh, r, &j.she, &j.ne);
     j.nint = nstrips - 2 * j.ne;
-    const long nt = (long)j.tiles_x * lines * nstrips;
+    const long nt = im.dims == 2 && j.tiles_x >= 2
+                        ? 4L * j.ne * j.she + 2L * j.ne * (j.tiles_x - 2) + (long)j.tiles_x * j.nint
+                        : (long)j.tiles_x * lines * nstrips;
     if (nt > 0x7FFFFFFFL) return fail(HRM_ENOTSUP, "too many tiles");
     j.ntiles = (int)nt;
     *job = j;

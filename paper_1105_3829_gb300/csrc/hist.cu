@@ -10,15 +10,20 @@ namespace hrm {
 // MINB = resident tiles per SM the register budget is sized for: 3 (up to
 // 168 registers) by default, 4 (128 registers) when the plan's shared memory
 // lets four tiles share an SM.
-template <typename T, int PPL, int CW, int MINB, int DIMS>
+template <typename T, int PPL, int CW, int MINB, int DIMS, bool GRP = false>
 __global__ void __launch_bounds__(BLOCK_THREADS, MINB) hist_kernel(HistJob job) {
     extern __shared__ __align__(16) unsigned char smem[];
-    hist_tile<T, PPL, CW, DIMS>(job, (int)blockIdx.x, smem);
+    hist_tile<T, PPL, CW, DIMS, GRP>(job, (int)blockIdx.x, smem);
 }
 
 template <typename T, int PPL, int CW, int MINB>
 static cudaError_t launch_one(const HistJob& job, size_t smem, cudaStream_t st) {
-    auto fn = job.dims == 3 ? hist_kernel<T, PPL, CW, MINB, 3> : hist_kernel<T, PPL, CW, MINB, 2>;
+    // 2D windows of at most 31 columns (8 or more 8-bit column records per
+    // packed-byte group of the direct sums) run the instance compiled for them
+    const bool grp = PPL == 1 && CW == 1 && MINB == 4 && job.dims == 2 && 255 / (2 * job.r + 1) >= 8;
+    auto fn = job.dims == 3 ? hist_kernel<T, PPL, CW, MINB, 3>
+                            : (grp ? hist_kernel<T, PPL, CW, MINB, 2, PPL == 1 && CW == 1 && MINB == 4>
+                                   : hist_kernel<T, PPL, CW, MINB, 2>);
     if (smem > 48 * 1024) {  // opt in per launch: the attribute is per device and cheap to set
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

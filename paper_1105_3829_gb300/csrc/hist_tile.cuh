@@ -493,7 +493,10 @@ __device__ __forceinline__ void note_used(Meta::Round& rb, const int (&slot)[PPL
     }
 }
 
-template <typename T, int PPL, int CW, int DIMS>
+// GRP: the kernel instance for small windows (at least 8 column records per
+// packed-byte group in the direct window sums, see below); other instances
+// keep the plain loop, which the compiler schedules better for them.
+template <typename T, int PPL, int CW, int DIMS, bool GRP = false>
 __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     constexpr int NT = BLOCK_THREADS;
     constexpr int TW = NT * PPL;
@@ -503,18 +506,30 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
     const int NC = TW + 2 * r;
     const int S = a.nslots;
     // Tile order (low ids start first).  2D with two or more tile columns:
-    // the edge strips (all columns), then the interior strips' first and last
-    // tile columns -- their windows are clamped in x, so they run slower --
-    // then the other interior tiles.  3D: x fastest, then the row, then the
+    // the edge strips' first and last tile columns one row per tile (at the
+    // image corners nearly every output's median needs its own tree node, so
+    // a corner row costs tens of interior rows: single-row tiles spread them
+    // over many blocks instead of making one 8-row tile the longest of the
+    // launch), then the other edge-strip tiles, then the interior strips'
+    // first and last tile columns -- their windows are clamped in x, so they
+    // run slower -- then the other interior tiles.  3D: x fastest, then the row, then the
     // strip.
-    int tx, yrow = 0, strip;
+    int tx, yrow = 0, strip, sub = -1;
     if (DIMS == 2 && a.tiles_x >= 2) {
-        const int nE = 2 * a.ne * a.tiles_x;
-        if (tile < nE) {
-            strip = tile / a.tiles_x;
-            tx = tile % a.tiles_x;
+        // the two corner tile columns of the edge strips: one tile per row
+        const int nC = 2 * (2 * a.ne * a.she);
+        const int nE = 2 * a.ne * (a.tiles_x - 2);
+        if (tile < nC) {
+            tx = (tile & 1) ? a.tiles_x - 1 : 0;
+            const int q = tile >> 1;
+            strip = q / a.she;
+            sub = q % a.she;
+        } else if (tile < nC + nE) {
+            const int k = tile - nC;
+            strip = k / (a.tiles_x - 2);
+            tx = 1 + k % (a.tiles_x - 2);
         } else {
-            int k = tile - nE;
+            int k = tile - nC - nE;
             if (k < 2 * a.nint) {
                 tx = (k & 1) ? a.tiles_x - 1 : 0;
                 strip = 2 * a.ne + (k >> 1);
@@ -549,6 +564,10 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
         } else {
             te = L - k * a.she;
             ts = te - a.she;
+        }
+        if (sub >= 0) {  // a single row of a corner tile column
+            ts += sub;
+            te = ts + 1;
         }
     } else {
         const int lo = a.ne * a.she;
@@ -643,6 +662,8 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
 
     // cost model (per block): one shared prefix of a node vs direct n-column sums
     const int prefix_cost = ((NC + NT - 1) / NT) * (CW == 1 ? 31 : 24) + 700;  // incl. two barriers
+    const int vpc = DIMS == 3 ? n * n : n;  // values per column record
+    const int grp = max(1, 255 / vpc);        // records summed as packed bytes per expansion
     const int direct_cost = n * (CW == 1 ? 24 : 14);
     uint32_t pass_id = 0;
 
@@ -941,7 +962,22 @@ __device__ void hist_tile(const HistJob& a, int tile, unsigned char* sm) {
                         const int xl = tid + NT * k;
                         const unsigned char* base = slots + (size_t)slot[k] * NC * 16 * CW;
                         uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                        for (int cx = xl; cx < xl + n; ++cx) rec_add<CW>(w, base + (size_t)cx * 16 * CW);
+                        if (GRP && CW == 1 && grp >= 8) {
+                            // 8-bit counters: a column holds vpc values, so up to 255 / vpc
+                            // records add as packed bytes without overflow; expand once per
+                            // group (small windows: at least 8 records per group)
+                            for (int cx = xl; cx < xl + n;) {
+                                const int ce = min(cx + grp, xl + n);
+                                uint4 b = make_uint4(0, 0, 0, 0);
+                                for (; cx < ce; ++cx) {
+                                    const uint4 q = *reinterpret_cast<const uint4*>(base + (size_t)cx * 16);
+                                    b.x += q.x; b.y += q.y; b.z += q.z; b.w += q.w;
+                                }
+                                acc_add(w, b);
+                            }
+                        } else {
+                            for (int cx = xl; cx < xl + n; ++cx) rec_add<CW>(w, base + (size_t)cx * 16 * CW);
+                        }
                         dig[k] = select16(w, K[k]);
                     }
                 } else {
