@@ -137,6 +137,11 @@ extern "C" int hrm_autotune(int dtype, int dims, int width, int height, int dept
     cudaFree(dst);
     if (synth) cudaFree(synth);
     if (rc) return rc;
+    if (bp.tile_width == 0 && bp.path == 0) {  // the default won: report (and cache) what it resolves to
+        const hrm_plan zero{0, 0, 0, 0};
+        const PlanH dp = resolve_plan(dtype, dims, width, height, D, radius, flags, di, &zero, false);
+        bp = hrm_plan{BLOCK_THREADS * dp.ppl, dp.sh, (int)((plan_smem(dp, radius) + 1023) / 1024), dp.path};
+    }
     plan_store(ProblemKey{dtype, dims, width, height, D, radius, flags}, bp);
     *best = bp;
     return HRM_OK;
