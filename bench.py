@@ -326,7 +326,8 @@ def run_secondary(args):
                     case["autotuned"] = {"p50_ms": float(np.median(t2)),
                                          "mpix_s": img.numel() / float(np.median(t2)) / 1e3,
                                          "plan": {"tile_width": plan.tile_width, "strip_height": plan.strip_height,
-                                                  "slot_kbytes": plan.slot_kbytes, "path": plan.path}}
+                                                  "slot_kbytes": plan.slot_kbytes, "path": plan.path,
+                         "tree": ("uniform", "adaptive")[plan.tree - 1] if plan.tree else None}}
                 res["r%d%s" % (r, "_adaptive" if ad else "")] = case
         clk.__exit__()
         value = float(np.mean([v.get("autotuned", v)["mpix_s"] for v in res.values()]))
@@ -458,7 +459,8 @@ def run_paper(args, hrm, inputs, torch, dev, flush):
             res["%s%s" % (name, "_adaptive" if ad else "")]["autotuned"] = {
                 "p50_ms": float(np.median(t2)), "mpix_s": img.numel() / float(np.median(t2)) / 1e3,
                 "plan": {"tile_width": plan.tile_width, "strip_height": plan.strip_height,
-                         "slot_kbytes": plan.slot_kbytes, "path": plan.path}}
+                         "slot_kbytes": plan.slot_kbytes, "path": plan.path,
+                         "tree": ("uniform", "adaptive")[plan.tree - 1] if plan.tree else None}}
     clk.__exit__()
     value = float(np.mean([v["mpix_s"] for v in res.values()]))
     _line("paper synthetic workloads at r=25 (4096^2): output Mpix/s (mean over cases)", "Mpix/s", value,

@@ -232,18 +232,27 @@ int hrm_batch_graph_destroy(hrm_batch_graph* g);
  *
  * The hierarchical kernels are parameterised by tile width (output columns
  * per 4-warp tile: 128 or 256, i.e. one or two outputs per thread), strip
- * length (rows or slices walked per tile) and the shared memory per tile for
- * cached tree nodes.  The tree itself is 16-ary at every level (one 16-byte
- * counter record per node and column): its shape comes from the data (the
- * uniform tree of the image's bit depth, or the adaptive top level), not from
- * the plan.  hrm_autotune times candidate plans
- * for one problem class on `stream` and caches the fastest; later calls of
+ * length (rows or slices walked per tile), the shared memory per tile for
+ * cached tree nodes, and the tree's top level.  Every level below the top is
+ * 16-ary (one 16-byte counter record per node and column); the top level is
+ * either 16 equal intervals over the image's value range (the uniform
+ * interval-occurrence tree, Section III) or the adaptive split: intervals of
+ * one power-of-16 width over the central range of a block-median estimate,
+ * which also fixes how many levels lie below (Section III-C).  A plan's
+ * `tree` field overrides the call's HRM_ADAPTIVE flag; the output is the same
+ * either way, only the speed differs.  hrm_autotune times candidate plans
+ * for one problem class on `stream` -- first the default plan and the
+ * default with the other top level, then tile widths, slot budgets and strip
+ * lengths under the faster top level -- and caches the fastest (the default
+ * unless another plan is at least 3 % faster); later calls of
  * the same class (dtype, dims, size, radius, flags) use it.  The timing runs
  * on `sample` (device pointer, the caller's pitches) when it is not NULL --
  * speed depends on the data, so a representative image is best -- and on a
  * synthetic image otherwise.  hrm_autotune allocates and frees its own output
  * (and synthetic input) buffers and blocks until the timing finishes.  The
- * cache is per process; hrm_plan_save / hrm_plan_load persist it as text.
+ * cache is per process; hrm_plan_save / hrm_plan_load persist it as text
+ * (one line per class; a line without the trailing tree field loads with
+ * tree 0).
  * Environment, read once per process: HRM_PLAN_CACHE=<file> loads a saved
  * plan file before the first call (a missing or malformed file is ignored);
  * HRM_FORCE_PATH=hist or =sortnet forces the histogram kernel or the
@@ -266,6 +275,8 @@ typedef struct {
     int strip_height;   /* output rows (2D) or slices (3D) per tile (0 = default) */
     int slot_kbytes;    /* shared memory per tile, KB (0 = default)            */
     int path;           /* 0 = auto, 1 = selection network, 2 = histogram     */
+    int tree;           /* top level: 0 = as the call's flags say,
+                           1 = uniform, 2 = adaptive (histogram path only)   */
 } hrm_plan;
 
 int hrm_autotune(int dtype, int dims, int width, int height, int depth, int radius,

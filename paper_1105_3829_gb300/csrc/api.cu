@@ -234,6 +234,7 @@ static void apply_plan(PlanH& p, const hrm_plan& hp, int dims, int W, int lines,
     p.sh = hp.strip_height > 0 ? std::min(hp.strip_height, walk)
                                : strip_length(dims, W, lines, walk, r, BLOCK_THREADS * p.ppl, plan_smem(p, r), di);
     if (hp.path == 1 || hp.path == 2) p.path = hp.path;
+    if (hp.tree == 1 || hp.tree == 2) p.tree = hp.tree;
 }
 
 // ---- node-cache feedback (2D histogram kernel, default plans only) ----------------
@@ -497,7 +498,7 @@ int filter_impl(const Image& im, int r, long rank, unsigned flags, int drop_bits
     Workspace* ws = nullptr;
     int rc = workspace_for(st, &ws);
     if (rc) return rc;
-    const bool adaptive = (flags & HRM_ADAPTIVE) != 0;
+    const bool adaptive = plan_adaptive(p, flags);
     const LevelDesc* desc = given;
     if (!desc && (es == 2 || adaptive)) {
         e = launch_levels(es, adaptive, im.src, im.sp, im.dims == 3 ? im.sslice : 0, im.W, im.H,
@@ -696,6 +697,7 @@ int hrm_get_plan(int dtype, int dims, int width, int height, int depth, int radi
     plan->strip_height = p.sh;
     plan->slot_kbytes = (int)((plan_smem(p, radius) + 1023) / 1024);
     plan->path = p.path;
+    plan->tree = p.path == 2 ? (plan_adaptive(p, flags) ? 2 : 1) : 0;
     return HRM_OK;
 }
 
@@ -706,6 +708,7 @@ int hrm_set_plan(int dtype, int dims, int width, int height, int depth, int radi
     if (plan->tile_width != 0 && plan->tile_width != 128 && plan->tile_width != 256)
         return fail(HRM_EINVAL, "tile_width must be 128 or 256");
     if (plan->path < 0 || plan->path > 2) return fail(HRM_EINVAL, "path must be 0, 1 or 2");
+    if (plan->tree < 0 || plan->tree > 2) return fail(HRM_EINVAL, "tree must be 0, 1 or 2");
     plan_store(ProblemKey{dtype, dims, width, height, depth, radius, flags}, *plan);
     return HRM_OK;
 }
@@ -715,13 +718,13 @@ int hrm_plan_save(const char* path) {
     std::ofstream f(path);
     if (!f) return fail(HRM_EINVAL, std::string("cannot write ") + path);
     std::lock_guard<std::mutex> lk(g_mu);
-    f << "# hrm plan cache v1: dtype dims width height depth radius flags tile_width strip_height slot_kbytes path\n";
+    f << "# hrm plan cache v2: dtype dims width height depth radius flags tile_width strip_height slot_kbytes path tree\n";
     for (auto& kv : g_plans) {
         auto& k = kv.first;
         auto& p = kv.second;
         f << std::get<0>(k) << ' ' << std::get<1>(k) << ' ' << std::get<2>(k) << ' ' << std::get<3>(k) << ' '
           << std::get<4>(k) << ' ' << std::get<5>(k) << ' ' << std::get<6>(k) << ' ' << p.tile_width << ' '
-          << p.strip_height << ' ' << p.slot_kbytes << ' ' << p.path << '\n';
+          << p.strip_height << ' ' << p.slot_kbytes << ' ' << p.path << ' ' << p.tree << '\n';
     }
     return f ? HRM_OK : fail(HRM_EINVAL, "write failed");
 }
@@ -740,6 +743,12 @@ int hrm_plan_load(const char* path) {
         if (!(is >> k.dtype >> k.dims >> k.width >> k.height >> k.depth >> k.radius >> k.flags >>
               p.tile_width >> p.strip_height >> p.slot_kbytes >> p.path))
             return fail(HRM_EINVAL, "malformed plan line: " + line);
+        std::string rest;
+        if (is >> rest) {  // the tree field (absent in lines written before it existed)
+            if (rest.size() != 1 || rest[0] < '0' || rest[0] > '2' || (is >> rest))
+                return fail(HRM_EINVAL, "malformed plan line: " + line);
+            p.tree = rest[0] - '0';
+        }
         plan_store(k, p);
         ++nload;
     }

@@ -1,12 +1,16 @@
 // autotune.cu -- timed search over kernel plans for one problem class.
 //
-// Candidates: the selection network vs the histogram kernel (2D radius <= 5),
-// tile width (128/256 outputs per tile), shared memory per tile for the node
-// cache (which trades cached nodes against resident tiles per SM), and strip
-// length (the default one-wave length and half of it: longer strips amortise
-// the per-strip start-up, shorter ones balance slow tiles).  Each candidate is timed with CUDA
-// events on the caller's stream; the fastest is cached for the class, the
-// default plan unless another is at least 3 % faster.
+// Candidates: the tree's top level (uniform over the value range, or the
+// adaptive power-of-16 split of Section III-C), the selection network vs the
+// histogram kernel (2D radius <= 5), tile width (128/256 outputs per tile),
+// shared memory per tile for the node cache (which trades cached nodes
+// against resident tiles per SM), and strip length (the default one-wave
+// length and half of it: longer strips amortise the per-strip start-up,
+// shorter ones balance slow tiles).  The top level is chosen first, on the
+// default geometry, and the geometry grid is then searched under it.  Each
+// candidate is timed with CUDA events on the caller's stream; the fastest is
+// cached for the class, the default plan unless another is at least 3 %
+// faster.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,11 +75,50 @@ extern "C" int hrm_autotune(int dtype, int dims, int width, int height, int dept
     Image im{dtype, dims, src, dst, sp, ss, pitch, slice, width, height, D};
     int rc = validate(im, radius, HRM_BORDER_REPLICATE, flags);
     const DeviceInfo& di = device_info();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+    }
+    // best of two timed runs after one warm-up (1e30 once rc is set)
+    auto time_plan = [&](const hrm_plan& cand) {
+        float ms = 1e30f;
+        if (!rc) rc = filter_impl(im, radius, -1, flags, 0, &cand, st);  // warm-up
+        for (int rep = 0; !rc && rep < 2; ++rep) {
+            cudaEventRecord(e0, st);
+            rc = filter_impl(im, radius, -1, flags, 0, &cand, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "autotune timing");
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = std::min(ms, t);
+        }
+        return rc ? 1e30f : ms;
+    };
+    // The default plan (all fields 0: the planner's choices, no feedback)
+    // is timed first; another plan replaces it only if it is at least
+    // KEEP_MARGIN faster, so timing noise between near-equal plans cannot
+    // pick a slower one.
+    constexpr float KEEP_MARGIN = 0.97f;
+    const hrm_plan zero{0, 0, 0, 0, 0};
+    const PlanH dp = rc ? PlanH{} : resolve_plan(dtype, dims, width, height, D, radius, flags, di, &zero, false);
+    const int own_tree = (flags & HRM_ADAPTIVE) ? 2 : 1;
+    hrm_plan bp = zero;
+    float best_ms = time_plan(zero) * KEEP_MARGIN;
+    int tree = own_tree;
+    if (!rc && dp.path == 2) {  // the other top level on the default geometry
+        const hrm_plan other{0, 0, 0, 0, 3 - own_tree};
+        const float ms = time_plan(other);
+        if (ms < best_ms) {
+            best_ms = ms;
+            bp = other;
+            tree = 3 - own_tree;
+        }
+    }
     std::vector<hrm_plan> cands;
-    const long n = 2L * radius + 1;
     const int cw = counter_width(dims, radius);
     if (!rc) {
-        if (dims == 2 && radius <= SORTNET_MAX_R2D) cands.push_back(hrm_plan{0, 0, 0, 1});
+        if (dims == 2 && radius <= SORTNET_MAX_R2D) cands.push_back(hrm_plan{0, 0, 0, 1, 0});
         const int lines = dims == 3 ? height : 1, walk = dims == 3 ? D : height;
         for (int tw : {BLOCK_THREADS, 2 * BLOCK_THREADS}) {
             if (tw > BLOCK_THREADS && width <= tw / 2) continue;
@@ -95,39 +138,15 @@ extern "C" int hrm_autotune(int dtype, int dims, int width, int height, int dept
                 for (int f : {2, 1}) {  // the default strip length and half of it
                     const int shf = std::max(8, sh / f);
                     if (f == 2 && shf == sh) continue;
-                    cands.push_back(hrm_plan{tw, shf, kb, 2});
+                    cands.push_back(hrm_plan{tw, shf, kb, 2, tree});
                 }
             }
         }
-        (void)n;
     }
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (!rc) {
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-    }
-    // The default plan (all fields 0: the planner's choices, no feedback)
-    // is timed first; another plan replaces it only if it is at least
-    // KEEP_MARGIN faster, so timing noise between near-equal plans cannot
-    // pick a slower one.
-    constexpr float KEEP_MARGIN = 0.97f;
-    if (!rc) cands.insert(cands.begin(), hrm_plan{0, 0, 0, 0});
-    float best_ms = 1e30f;
-    hrm_plan bp{0, 0, 0, 0};
     for (size_t i = 0; !rc && i < cands.size(); ++i) {
-        rc = filter_impl(im, radius, -1, flags, 0, &cands[i], st);  // warm-up
-        float ms = 1e30f;
-        for (int rep = 0; !rc && rep < 2; ++rep) {
-            cudaEventRecord(e0, st);
-            rc = filter_impl(im, radius, -1, flags, 0, &cands[i], st);
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "autotune timing");
-            float t = 0;
-            cudaEventElapsedTime(&t, e0, e1);
-            ms = std::min(ms, t);
-        }
-        if (!rc && (i == 0 ? true : ms < best_ms)) {
-            best_ms = i == 0 ? ms * KEEP_MARGIN : ms;
+        const float ms = time_plan(cands[i]);
+        if (ms < best_ms) {
+            best_ms = ms;
             bp = cands[i];
         }
     }
@@ -137,10 +156,11 @@ extern "C" int hrm_autotune(int dtype, int dims, int width, int height, int dept
     cudaFree(dst);
     if (synth) cudaFree(synth);
     if (rc) return rc;
-    if (bp.tile_width == 0 && bp.path == 0) {  // the default won: report (and cache) what it resolves to
-        const hrm_plan zero{0, 0, 0, 0};
-        const PlanH dp = resolve_plan(dtype, dims, width, height, D, radius, flags, di, &zero, false);
-        bp = hrm_plan{BLOCK_THREADS * dp.ppl, dp.sh, (int)((plan_smem(dp, radius) + 1023) / 1024), dp.path};
+    if (bp.tile_width == 0 && bp.path == 0) {  // a default-geometry plan won: report (and cache) what it resolves to
+        const int t = bp.tree;
+        const PlanH rp = resolve_plan(dtype, dims, width, height, D, radius, flags, di, &bp, false);
+        bp = hrm_plan{BLOCK_THREADS * rp.ppl, rp.sh, (int)((plan_smem(rp, radius) + 1023) / 1024), rp.path,
+                      rp.path == 2 ? (t ? t : own_tree) : 0};
     }
     plan_store(ProblemKey{dtype, dims, width, height, D, radius, flags}, bp);
     *best = bp;

@@ -271,13 +271,14 @@ static int plan_batch(const hrm_job* jobs, int njobs, const BatchDev& dev, Batch
             t.cost = 2.0;
         } else {
             const LevelDesc* desc = given;
-            if (!desc && (es == 2 || (flags & HRM_ADAPTIVE))) {
+            const bool adaptive = plan_adaptive(p, flags);
+            if (!desc && (es == 2 || adaptive)) {
                 const int li = (int)bp.levels.size();
                 if (li >= dev.cap) return fail(HRM_ENOTSUP, "too many jobs for the batch buffer");
                 LevelItem L{(const unsigned char*)im.src, im.sp, im.dims == 3 ? im.sslice : 0, im.W, im.H,
-                            im.D, es, dev.descs + li, (flags & HRM_ADAPTIVE) ? 1 : 0, 0};
+                            im.D, es, dev.descs + li, adaptive ? 1 : 0, 0};
                 if (!bp.levels.push_back(L)) return fail(HRM_ENOTSUP, "too many jobs");
-                if ((flags & HRM_ADAPTIVE) && !bp.adaptive.push_back(li)) return fail(HRM_ENOTSUP, "too many jobs");
+                if (adaptive && !bp.adaptive.push_back(li)) return fail(HRM_ENOTSUP, "too many jobs");
                 desc = dev.descs + li;
             }
             t.it.kind = ITEM_HIST;

@@ -54,7 +54,13 @@ struct PlanH {
     int cw;       // counter width (bytes)
     int ring;     // stage the last n+1 input rows in shared memory (2D)
     int es;       // element size (bytes)
+    int tree;     // top level: 0 = as the call's flags say, 1 = uniform, 2 = adaptive
 };
+// Whether a histogram call builds the adaptive top level: the plan's tree
+// choice, else the call's HRM_ADAPTIVE flag.
+inline bool plan_adaptive(const PlanH& p, unsigned flags) {
+    return p.tree ? p.tree == 2 : (flags & HRM_ADAPTIVE) != 0;
+}
 struct ProblemKey {
     int dtype, dims, width, height, depth, radius;
     unsigned flags;

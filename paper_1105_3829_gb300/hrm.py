@@ -48,7 +48,7 @@ class hrm_job(C.Structure):
 
 class hrm_plan(C.Structure):
     _fields_ = [("tile_width", C.c_int), ("strip_height", C.c_int), ("slot_kbytes", C.c_int),
-                ("path", C.c_int)]
+                ("path", C.c_int), ("tree", C.c_int)]
 
 
 class hrm_request(C.Structure):

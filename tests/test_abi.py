@@ -101,14 +101,25 @@ def test_validation_without_device(lib):
 
 def test_plan_cache_roundtrip(lib, tmp_path):
     from paper_1105_3829_gb300 import hrm
-    p = hrm.hrm_plan(128, 96, 40, 2)
+    p = hrm.hrm_plan(128, 96, 40, 2, 2)
     hrm.set_plan(2, 2, 4096, 4096, 1, 15, p)
     path = str(tmp_path / "plans.txt")
     assert hrm.hrm_plan_save(path.encode()) == 0
     text = open(path).read()
-    assert "2 2 4096 4096 1 15 0 128 96 40 2" in text
-    open(path, "a").write("1 2 512 512 1 3 0 64 32 20 2\n")
+    assert "2 2 4096 4096 1 15 0 128 96 40 2 2\n" in text
+    # a line without the tree field (older files) and one with it
+    open(path, "a").write("1 2 512 512 1 3 0 64 32 20 2\n1 2 512 512 1 4 1 128 32 20 2 1\n")
     assert hrm.hrm_plan_load(path.encode()) == 0
+    got = hrm.get_plan(1, 2, 512, 512, 1, 3)
+    assert (got.tile_width, got.strip_height, got.slot_kbytes, got.path, got.tree) == (64, 32, 20, 2, 0)
+    got = hrm.get_plan(1, 2, 512, 512, 1, 4, adaptive=True)
+    assert (got.tile_width, got.path, got.tree) == (128, 2, 1)
+    got = hrm.get_plan(2, 2, 4096, 4096, 1, 15)
+    assert (got.tile_width, got.strip_height, got.slot_kbytes, got.path, got.tree) == (128, 96, 40, 2, 2)
+    for line in ("1 2 512 512 1 5 0 128 32 20 2 3\n", "1 2 512 512 1 5 0 128 32 20 2 1 7\n"):
+        bad_file = tmp_path / "bad.txt"
+        bad_file.write_text(line)
+        assert hrm.hrm_plan_load(str(bad_file).encode()) == hrm.HRM_EINVAL
     bad = hrm.hrm_plan(100, 0, 0, 0)
     with pytest.raises(hrm.HRMError):
         hrm.set_plan(1, 2, 10, 10, 1, 3, bad)
@@ -194,3 +205,4 @@ def test_server_topology_and_graph_arguments_without_device(lib):
     refused(lambda: hrm.hrm_get_plan(2, 4, 64, 64, 1, 5, 0, ctypes.byref(p)))            # dims
     refused(lambda: hrm.hrm_set_plan(2, 2, 64, 64, 1, 5, 0, ctypes.byref(hrm.hrm_plan(64, 0, 0, 0))))   # tile width
     refused(lambda: hrm.hrm_set_plan(2, 2, 64, 64, 1, 5, 0, ctypes.byref(hrm.hrm_plan(0, 0, 0, 3))))    # path
+    refused(lambda: hrm.hrm_set_plan(2, 2, 64, 64, 1, 5, 0, ctypes.byref(hrm.hrm_plan(0, 0, 0, 2, 3))))  # tree

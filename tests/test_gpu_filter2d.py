@@ -231,10 +231,11 @@ def test_autotune_plans_keep_parity(hrm, oracle):
     for r, adaptive in ((3, False), (9, False), (9, True), (24, False)):
         plan = hrm.autotune(src, r, adaptive=adaptive)
         assert plan.path in (1, 2)
-        assert plan.tile_width in (0, 128, 256)
+        assert plan.tile_width in ((0, 128, 256) if plan.path == 1 else (128, 256))  # networks have no tiles
+        assert plan.tree in ((0,) if plan.path == 1 else (1, 2))
         got = hrm.get_plan(2, 2, 420, 180, 1, r, adaptive=adaptive)
-        assert (got.tile_width, got.strip_height, got.slot_kbytes, got.path) == \
-            (plan.tile_width, plan.strip_height, plan.slot_kbytes, plan.path)
+        assert (got.tile_width, got.strip_height, got.slot_kbytes, got.path, got.tree) == \
+            (plan.tile_width, plan.strip_height, plan.slot_kbytes, plan.path, plan.tree)
         out = _host(hrm.filter2d(src, r, adaptive=adaptive))
         np.testing.assert_array_equal(out, oracle.median2d(img, r))
     vol = inputs.xray12_volume(20, 24, 70, seed=3)
@@ -294,3 +295,30 @@ def test_node_cache_feedback(hrm, oracle):
                 (name, before.slot_kbytes, after.slot_kbytes)
         else:
             assert after.slot_kbytes == before.slot_kbytes, (name, after.slot_kbytes)
+
+
+def test_tree_plans_keep_parity(hrm, oracle):
+    """A plan's top-level choice (1 = uniform, 2 = the adaptive power-of-16
+    split) overrides the call's adaptive flag, in single calls and in
+    batches; the output stays the exact median either way (Section III-C:
+    the topology changes the speed only)."""
+    from paper_1105_3829_gb300 import inputs
+    img16 = inputs.lowkey16_u16(150, 333, seed=44)
+    img8 = (inputs.lowkey16_u16(97, 301, seed=45) >> 4).astype(np.uint8)
+    for img, code in ((img16, hrm.HRM_U16), (img8, hrm.HRM_U8)):
+        H, W = img.shape
+        src = _dev(img)
+        for r in (7, 23):
+            exp = oracle.median2d(img, r)
+            for adaptive in (False, True):
+                for tree in (1, 2):
+                    hrm.set_plan(code, 2, W, H, 1, r, hrm.hrm_plan(0, 0, 0, 2, tree), adaptive=adaptive)
+                    try:
+                        assert hrm.get_plan(code, 2, W, H, 1, r, adaptive=adaptive).tree == tree
+                        np.testing.assert_array_equal(_host(hrm.filter2d(src, r, adaptive=adaptive)), exp)
+                        dst = torch.empty_like(src)
+                        hrm.filter_batch([hrm.make_job(src, dst, r, adaptive=adaptive)])
+                        hrm.device_status()
+                        np.testing.assert_array_equal(_host(dst), exp)
+                    finally:
+                        hrm.set_plan(code, 2, W, H, 1, r, hrm.hrm_plan(0, 0, 0, 0, 0), adaptive=adaptive)
