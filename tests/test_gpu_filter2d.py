@@ -322,3 +322,31 @@ def test_tree_plans_keep_parity(hrm, oracle):
                         np.testing.assert_array_equal(_host(dst), exp)
                     finally:
                         hrm.set_plan(code, 2, W, H, 1, r, hrm.hrm_plan(0, 0, 0, 0, 0), adaptive=adaptive)
+
+
+@pytest.mark.parametrize("r", [6, 17, 31, 32])
+def test_small_node_caches_many_rounds(hrm, oracle, r):
+    """Full-range 16-bit noise: a 16-value node holds one or two window
+    values, so a tile row visits far more nodes than a small node cache
+    holds and levels take several rounds of node builds (slots reassigned
+    between rounds of one level).  Small caches without the shared-memory row
+    ring (builds read global memory) and larger ones with it; the median,
+    extreme and interior ranks, and the truncated median all match the
+    oracle."""
+    rng = np.random.default_rng(900 + r)
+    H, W = 70 + r, 260
+    img = rng.integers(0, 65536, size=(H, W)).astype(np.uint16)
+    src = _dev(img)
+    n = 2 * r + 1
+    exp = oracle.median2d(img, r)
+    for kb in (32, 96):
+        hrm.set_plan(hrm.HRM_U16, 2, W, H, 1, r, hrm.hrm_plan(128, 0, kb, 2, 1))
+        try:
+            np.testing.assert_array_equal(_host(hrm.filter2d(src, r)), exp)
+            for rank in (0, n * n - 1, (n * n) // 5):
+                np.testing.assert_array_equal(_host(hrm.rank_filter2d(src, r, rank)),
+                                              oracle.median2d(img, r, rank=rank))
+            np.testing.assert_array_equal(_host(hrm.filter2d_lowprec(src, r, 5)), exp & np.uint16(0xFFE0))
+            hrm.device_status()
+        finally:
+            hrm.set_plan(hrm.HRM_U16, 2, W, H, 1, r, hrm.hrm_plan(0, 0, 0, 0, 0))
