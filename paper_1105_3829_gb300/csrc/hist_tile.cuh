@@ -160,6 +160,7 @@ __device__ __forceinline__ int ring_idx(int u, int M) { return (u + M) % M; }
 struct NodeRange {
     int level;
     uint32_t lo, hi;
+    uint32_t width;  // hi - lo (levels > 0)
     int dshift;
 };
 
@@ -178,13 +179,8 @@ __device__ __forceinline__ NodeRange node_range(const Meta& m, uint32_t key) {
         nr.hi = min(nr.lo + (1u << top), m.e[c + 1]);
         nr.dshift = top - b;
     }
+    nr.width = nr.hi - nr.lo;
     return nr;
-}
-
-__device__ __forceinline__ int node_digit(const Meta& m, const NodeRange& nr, uint32_t v) {
-    if (nr.level == 0) return coarse_of(m, v);
-    if (v < nr.lo || v >= nr.hi) return -1;
-    return (int)((v - nr.lo) >> nr.dshift);
 }
 
 // Build the records of the m.nbuild build entries (slot, column range) at walk
@@ -210,10 +206,21 @@ __device__ void build_slots(const HistJob& a, const Geo& g, const Meta& m, unsig
         const int c0 = 2 * (((int)m.build_lo[b] >> 1) + (it - (int)m.build_off[b]));
         const NodeRange nr = node_range(m, m.build_key[b]);
         uint32_t cnt0[8] = {0, 0, 0, 0, 0, 0, 0, 0}, cnt1[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        // Below the root a value belongs to the node iff (v - lo) < width
+        // (unsigned).  Nodes deep in a wide distribution hold few of a
+        // column's values, so the counting sits behind one test per pair.
         auto count2 = [&](uint32_t v0, uint32_t v1) {
-            const int d0 = node_digit(m, nr, v0), d1 = node_digit(m, nr, v1);
-            if (d0 >= 0) reg_count<CW>(cnt0, d0);
-            if (d1 >= 0) reg_count<CW>(cnt1, d1);
+            if (nr.level == 0) {
+                reg_count<CW>(cnt0, coarse_of(m, v0));
+                reg_count<CW>(cnt1, coarse_of(m, v1));
+                return;
+            }
+            const uint32_t e0 = v0 - nr.lo, e1 = v1 - nr.lo;
+            const bool in0 = e0 < nr.width, in1 = e1 < nr.width;
+            if (__builtin_expect(in0 || in1, 0)) {
+                if (in0) reg_count<CW>(cnt0, (int)(e0 >> nr.dshift));
+                if (in1) reg_count<CW>(cnt1, (int)(e1 >> nr.dshift));
+            }
         };
         if (ring) {
             const int M = 2 * r + 2;
