@@ -617,6 +617,11 @@ def main():
     smi_index = vis.split(",")[local].strip() if vis else str(local)
     with ClockSampler(smi_index) as clk:
         t_wall0 = time.perf_counter()
+        # One untimed fill ahead of the first step: the timed steps start from
+        # an empty GPU queue, and a host stall between a launch's start event
+        # and the launch itself would be timed as idle GPU.  Later steps queue
+        # behind the previous step's r = 50 call.
+        flush.fill_(0)
         for k in range(args.steps):
             step(ev[k])
         torch.cuda.synchronize()
